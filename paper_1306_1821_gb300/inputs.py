@@ -1,0 +1,160 @@
+"""Seeded synthetic surveys (inputs only: none of the sampler's arithmetic).
+
+Stand-ins for the paper's SDSS-DR7-like mock (Sec. 5), whose mask, Schechter
+selection and Eisenstein-Hu spectrum are not available here:
+
+  * spectrum P(k) = A k (1 + (k / 0.02)^2)^-2, k in h/Mpc, with A chosen so the
+    voxel variance (1/V) sum_{k != 0} P(k) over the grid is 0.5;
+  * true field delta = IFFT(sqrt(P(k)/V_cell) FFT(xi)) with xi white noise
+    (FFT forward unnormalised, inverse 1/N_vox, the App. C.1 convention);
+  * observer at the box centre, voxel centres at (i + 1/2) dx - L/2; angular
+    mask a spherical cap about +z, cos(theta) >= 1 - 2 f_sky; R = 0 beyond L/2;
+  * radial selection linear (1 - r / (L/2)) or Gaussian exp(-(r / r0)^2);
+  * counts N^l ~ Poisson(R^l Nbar^l max(0, 1 + b^l delta)) (the data model of
+    Eq. data_model with Poisson rather than Gaussian noise).
+
+Everything is drawn from numpy's PCG64 with a fixed seed, so each named
+workload is reproducible bit for bit.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    N: int
+    box: float
+    n_bins: int
+    b: list
+    nbar: list
+    f_sky: float
+    radial: str            # "linear" or "gauss"
+    r0: float = 350.0
+    n_leapfrog: int = 10
+    eps_max: float = 0.3
+    jump: bool = False
+    jump_leapfrog: int = 10
+    jump_eps_max: float = 0.05
+    seed: int = 0
+    alpha: float = 1.0
+    fixed_bias: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_sub(self):
+        return len(self.b)
+
+
+def _six_nbar():
+    return [8.0 * (1.0 / 16.0) ** (l / 5.0) for l in range(6)]
+
+
+SIX_B = [1.0, 1.1, 1.2, 1.35, 1.5, 1.65]
+
+WORKLOADS = {
+    # 32^3, L = 500 Mpc/h, one subsample, 40% sky with linear radial fall-off
+    "survey32": Workload("survey32", 32, 500.0, 16, [1.2], [5.0], 0.4, "linear",
+                         n_leapfrog=10, eps_max=0.35),
+    # 128^3, L = 750 Mpc/h, six luminosity subsamples, 25% sky, exp(-(r/350)^2)
+    "survey128": Workload("survey128", 128, 750.0, 16, SIX_B, _six_nbar(), 0.25, "gauss",
+                          n_leapfrog=10, eps_max=0.3),
+    # 256^3, L = 1000 Mpc/h, six subsamples, 32 bins, 20 leapfrog steps, jump on
+    "survey256": Workload("survey256", 256, 1000.0, 32, SIX_B, _six_nbar(), 0.25, "gauss",
+                          n_leapfrog=20, eps_max=0.25, jump=True, jump_leapfrog=10),
+}
+
+
+def small_workload(N, box=None, n_bins=4, n_sub=1, f_sky=0.5, seed=0, **kw):
+    """A small survey for parity tests (same recipe, any grid size)."""
+    box = float(box if box is not None else 500.0 * N / 32.0)
+    b = SIX_B[:n_sub]
+    nbar = _six_nbar()[:n_sub]
+    return Workload(f"small{N}", N, box, n_bins, b, nbar, f_sky, "gauss", r0=0.7 * box / 2.0,
+                    seed=seed, **kw)
+
+
+def spectrum_shape(k):
+    k = np.asarray(k, dtype=np.float64)
+    return k * (1.0 + (k / 0.02) ** 2) ** -2
+
+
+def wavenumbers(N, box):
+    """|k| on the half-spectrum grid [N][N][N/2+1] (h/Mpc)."""
+    i = np.arange(N)
+    n = np.where(i <= N // 2, i, i - N).astype(np.float64)
+    nz = np.arange(N // 2 + 1, dtype=np.float64)
+    n2 = n[:, None, None] ** 2 + n[None, :, None] ** 2 + nz[None, None, :] ** 2
+    return 2.0 * np.pi * np.sqrt(n2) / box
+
+
+def amplitude(N, box, variance=0.5):
+    """A such that (1/V) sum over all non-DC grid modes of P(k) equals `variance`."""
+    k = wavenumbers(N, box)
+    w = np.full(k.shape, 2.0)
+    w[:, :, 0] = 1.0
+    w[:, :, N // 2] = 1.0
+    s = np.sum(w * spectrum_shape(k))
+    return variance * box ** 3 / s
+
+
+def true_spectrum(k, N, box):
+    return amplitude(N, box) * spectrum_shape(k)
+
+
+def bin_centre_spectrum(N, box, n_bins):
+    """The true spectrum at the centres of n_bins linear |n| bins over (0, sqrt(3) N/2]."""
+    edges = np.sqrt(3.0) * N / 2.0 / n_bins
+    nc = (np.arange(n_bins) + 0.5) * edges
+    return true_spectrum(2.0 * np.pi * nc / box, N, box)
+
+
+def response(N, box, f_sky, radial, r0=350.0):
+    """Survey response R (float32 [N]^3): spherical cap times radial selection."""
+    dx = box / N
+    c = (np.arange(N) + 0.5) * dx - box / 2.0
+    x, y, z = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z)
+    cos_t = np.where(r > 0, z / np.maximum(r, 1e-300), 1.0)
+    cap = cos_t >= 1.0 - 2.0 * f_sky
+    rmax = box / 2.0
+    if radial == "linear":
+        sel = np.maximum(0.0, 1.0 - r / rmax)
+    else:
+        sel = np.exp(-(r / r0) ** 2)
+    R = np.where(cap & (r <= rmax), sel, 0.0)
+    return R.astype(np.float32)
+
+
+def make_survey(wl: Workload, seed=None):
+    """(delta_true float64 [N]^3, counts int32 [n_sub,N,N,N], R float32 [n_sub,N,N,N])."""
+    seed = wl.seed if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = wl.N
+    xi = rng.standard_normal((N, N, N))
+    k = wavenumbers(N, wl.box)
+    vc = (wl.box / N) ** 3
+    amp = np.sqrt(true_spectrum(k, N, wl.box) / vc)
+    amp[0, 0, 0] = 0.0
+    delta = np.fft.irfftn(amp * np.fft.rfftn(xi), s=(N, N, N), axes=(0, 1, 2))
+    R1 = response(N, wl.box, wl.f_sky, wl.radial, wl.r0)
+    R = np.broadcast_to(R1, (wl.n_sub, N, N, N)).copy()
+    counts = np.empty((wl.n_sub, N, N, N), dtype=np.int32)
+    for l in range(wl.n_sub):
+        lam = R[l].astype(np.float64) * wl.nbar[l] * np.maximum(0.0, 1.0 + wl.b[l] * delta)
+        counts[l] = rng.poisson(lam).astype(np.int32)
+    return delta, counts, R
+
+
+def initial_state(wl: Workload):
+    """Starting point: delta_hat = 0, P at the bin centres, b and Nbar at the truth."""
+    P = bin_centre_spectrum(wl.N, wl.box, wl.n_bins)
+    return P, np.array(wl.b, dtype=np.float64), np.array(wl.nbar, dtype=np.float64)
+
+
+def random_spectrum(N, n_bins, seed, scale=1.0):
+    """A seeded random half spectrum (complex128 [N][N][N/2+1]) of a real field."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.standard_normal((N, N, N)) * scale
+    return np.fft.rfftn(x)

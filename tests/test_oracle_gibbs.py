@@ -1,0 +1,167 @@
+"""Pins of the oracle's conditional samplers (Secs. 3.4-3.6, 4.2, 4.3, Apps. A-C)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from oracle import gibbs, grid, model
+from paper_1306_1821_gb300 import inputs
+
+
+def survey(N=4, n_sub=2, n_bins=2, seed=2, f_sky=0.8):
+    wl = inputs.small_workload(N, n_bins=n_bins, n_sub=n_sub, f_sky=f_sky, seed=seed)
+    delta_true, counts, R = inputs.make_survey(wl)
+    g = grid.Geometry(N, wl.box, n_bins)
+    return wl, g, delta_true, counts, R
+
+
+def test_bin_power_definition():
+    wl, g, d, counts, R = survey(N=8, n_bins=3)
+    dh = grid.forward(d)
+    s = gibbs.bin_power(g, dh)
+    full = np.fft.fftn(d)
+    i = np.arange(8)
+    n = np.where(i <= 4, i, i - 8)
+    n2 = (n[:, None, None] ** 2 + n[None, :, None] ** 2 + n[None, None, :] ** 2)
+    b = grid.bin_of_n2(n2, 8, 3)
+    for m in range(3):
+        assert s[m] == pytest.approx(g.Vc / g.Nv * np.sum(np.abs(full[b == m]) ** 2), rel=1e-12)
+
+
+def test_power_draw_is_inverse_gamma():
+    wl, g, d, counts, R = survey(N=8, n_bins=3)
+    dh = grid.forward(d)
+    alpha = 1.0
+    draws_ = np.array([gibbs.sample_power(g, dh, alpha, 3, it)[0] for it in range(2000)])
+    sigma = gibbs.bin_power(g, dh)
+    for m in range(3):
+        beta = g.n_modes[m] + 2 * alpha - 2
+        ref = stats.invgamma(a=beta / 2.0, scale=sigma[m] / 2.0)
+        assert stats.kstest(draws_[:, m], ref.cdf).pvalue > 1e-3
+    # Eq. INVERSE_GAMMA with a flat prior (alpha = 0) has shape n_m/2 - 1
+    d0 = np.array([gibbs.sample_power(g, dh, 0.0, 4, it)[0][2] for it in range(2000)])
+    ref0 = stats.invgamma(a=(g.n_modes[2] - 2) / 2.0, scale=sigma[2] / 2.0)
+    assert stats.kstest(d0, ref0.cdf).pvalue > 1e-3
+
+
+def literal_loglik(delta, counts, R, b, nbar, l):
+    """log of Eq. LH_per_dataset for subsample l, voxels with R > 0 (normalisation included)."""
+    obs = R[l] > 0
+    r = R[l][obs].astype(np.float64)
+    res = counts[l][obs] - nbar * r * (1.0 + b * delta[obs])
+    return -0.5 * np.sum(res * res / (nbar * r)) - 0.5 * obs.sum() * math.log(2 * math.pi * nbar) \
+        - 0.5 * np.sum(np.log(r))
+
+
+def test_bias_conditional_against_quadrature():
+    wl, g, d, counts, R = survey(N=4, n_sub=2)
+    delta = d * 0.9
+    nbar = np.array(wl.nbar)
+    sums = gibbs.subsample_sums(delta, counts, R)
+    consts = gibbs.data_constants(counts, R)
+    l = 1
+    # posterior of b_1 by brute-force quadrature of Eq. galaxybias_post (flat prior)
+    bs = np.linspace(-6, 8, 4001)
+    lp = np.array([literal_loglik(delta, counts, R, bb, nbar[l], l) for bb in bs])
+    w = np.exp(lp - lp.max())
+    Z = integrate.trapezoid(w, bs)
+    mean = integrate.trapezoid(w * bs, bs) / Z
+    var = integrate.trapezoid(w * (bs - mean) ** 2, bs) / Z
+    xs = np.array([gibbs.sample_bias_norm(delta, sums, consts, wl.b, nbar, 0, 6, it)[0][l] for it in range(3000)])
+    assert abs(xs.mean() - mean) < 4 * math.sqrt(var / len(xs))
+    assert xs.var() == pytest.approx(var, rel=0.1)
+    # fixed index is untouched
+    b_new, _ = gibbs.sample_bias_norm(delta, sums, consts, wl.b, nbar, 0, 6, 0)
+    assert b_new[0] == wl.b[0]
+
+
+def test_nbar_conditional_against_quadrature():
+    wl, g, d, counts, R = survey(N=4, n_sub=2)
+    delta = d * 0.9
+    b = np.array(wl.b)
+    sums = gibbs.subsample_sums(delta, counts, R)
+    consts = gibbs.data_constants(counts, R)
+    l = 0
+    # Eq. nmean_post with a flat prior: likelihood of Eq. LH_per_dataset in Nbar
+    xs_grid = np.linspace(0.5, 25.0, 6001)
+    lp = np.array([literal_loglik(delta, counts, R, b[l], x, l) for x in xs_grid])
+    w = np.exp(lp - lp.max())
+    Z = integrate.trapezoid(w, xs_grid)
+    mean = integrate.trapezoid(w * xs_grid, xs_grid) / Z
+    var = integrate.trapezoid(w * (xs_grid - mean) ** 2, xs_grid) / Z
+    # hold b fixed for the check (fixed index = l), so only Nbar moves
+    out = np.array([gibbs.sample_bias_norm(delta, sums, consts, b, wl.nbar, l, 8, it)[1][l] for it in range(3000)])
+    assert abs(out.mean() - mean) < 4 * math.sqrt(var / len(out))
+    assert out.var() == pytest.approx(var, rel=0.1)
+
+
+def test_subsample_sums_and_constants():
+    wl, g, d, counts, R = survey(N=4, n_sub=2)
+    sums = gibbs.subsample_sums(d, counts, R)
+    sR, sB, nobs = gibbs.data_constants(counts, R)
+    for l in range(2):
+        S1 = S2 = S3 = 0.0
+        for idx in np.ndindex(4, 4, 4):
+            r = float(R[l][idx])
+            if r > 0:
+                S1 += counts[l][idx] * d[idx]
+                S2 += r * d[idx]
+                S3 += r * d[idx] ** 2
+        assert np.allclose(sums[l], [S1, S2, S3], rtol=1e-12)
+        assert nobs[l] == np.sum(R[l] > 0)
+
+
+@pytest.mark.slow
+def test_jump_leaves_conditional_of_P_invariant():
+    # 4^3 grid, one bin: theta = ln P is one-dimensional and the whitened field
+    # u is invariant under the move, so a chain of jumps must sample
+    # p(theta | u, d) ~ exp((1 - alpha) theta) exp(-lik(delta(u, theta)))
+    # (Eq. spec_posterior_MIXING_1 with the power-law prior); compare with 1-D quadrature.
+    wl, g, d, counts, R = survey(N=4, n_sub=1, n_bins=1, seed=5, f_sky=0.9)
+    b = np.array(wl.b)
+    nbar = np.array(wl.nbar)
+    a, c = model.local_fields(counts, R, b, nbar)
+    abar = a.mean()
+    alpha = 1.0
+    P0 = np.array([inputs.bin_centre_spectrum(4, wl.box, 1)[0]])
+    dh0 = grid.forward(d)
+    dh0[0, 0, 0] = 0
+    ths = np.linspace(math.log(P0[0]) - 8, math.log(P0[0]) + 8, 3001)
+    lp = np.array([-gibbs.jump_potential_grad(g, dh0, P0, np.array([t]), a, c, alpha)[0] for t in ths])
+    w = np.exp(lp - lp.max())
+    Z = integrate.trapezoid(w, ths)
+    mean = integrate.trapezoid(w * ths, ths) / Z
+    var = integrate.trapezoid(w * (ths - mean) ** 2, ths) / Z
+    dh, P = dh0.copy(), P0.copy()
+    out = []
+    acc = 0
+    for it in range(3000):
+        dh, P, info = gibbs.jump_move(g, dh, P, a, c, abar, alpha, 6, 0.5, 21, it, P_ref=P0)
+        acc += info["accepted"]
+        out.append(math.log(P[0]))
+    out = np.array(out[200:])
+    assert acc > 1500
+    nb = 20
+    bm = out[: (len(out) // nb) * nb].reshape(nb, -1).mean(1)
+    se = bm.std(ddof=1) / math.sqrt(nb)
+    assert abs(out.mean() - mean) < 4.5 * max(se, 1e-3)
+    assert out.var() == pytest.approx(var, rel=0.15)
+    # the whitened field is unchanged by the jumps
+    u0 = dh0 / math.sqrt(P0[0])
+    assert np.allclose(dh / math.sqrt(P[0]), u0, atol=1e-10)
+
+
+def test_jump_gradient_matches_finite_differences():
+    wl, g, d, counts, R = survey(N=8, n_sub=2, n_bins=3)
+    a, c = model.local_fields(counts, R, np.array(wl.b), np.array(wl.nbar))
+    dh0 = grid.forward(d)
+    P0 = inputs.bin_centre_spectrum(8, wl.box, 3)
+    th = np.log(P0) + np.array([0.2, -0.1, 0.3])
+    _, gr = gibbs.jump_potential_grad(g, dh0, P0, th, a, c, 0.5)
+    for m in range(3):
+        e = np.zeros(3)
+        e[m] = 1e-5
+        fp = gibbs.jump_potential_grad(g, dh0, P0, th + e, a, c, 0.5)[0]
+        fm = gibbs.jump_potential_grad(g, dh0, P0, th - e, a, c, 0.5)[0]
+        assert gr[m] == pytest.approx((fp - fm) / 2e-5, rel=1e-6, abs=1e-8)
