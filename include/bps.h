@@ -1,0 +1,200 @@
+/*
+ * bps.h - C ABI of the GB300 sampler for joint Bayesian inference of a 3D
+ * density field, its power spectrum, galaxy biases and normalisations
+ * (Jasche & Wandelt, arXiv:1306.1821).
+ *
+ * Scope: the data-parallel hot path of the paper's multiple-block sampler
+ * (Sec. 3.2, Eq. multiblock; Fig. 1):
+ *   - the Hybrid Monte Carlo move of the density field (Sec. 4.1, Eqs.
+ *     Potential..acceptance_rule, Wiener_Posterior_psi, Wiener_Posterior_force,
+ *     Mass_matrix), whose force alternates 3D real-to-complex FFTs that apply the
+ *     inverse-power-spectrum prior per mode with the voxel-local likelihood of
+ *     the data model N = Nbar R (1 + b delta) + noise (Eq. data_model,
+ *     Eq. LH_all_dataset);
+ *   - the k-binned power and per-subsample reductions that feed the power
+ *     spectrum draw (Sec. 3.4, Eq. INVERSE_GAMMA; Sec. 4.2, Eq. XI_SQUARE), the
+ *     bias draw (Sec. 3.5, App. B), the normalisation draw (Sec. 3.6, Eq.
+ *     GIG_post, App. A) and the deterministic P-delta jump (Sec. 4.3, Eqs.
+ *     det_trans, mixing_pdf; App. C).
+ *
+ * Conventions (App. C.1): forward transform unnormalised, inverse 1/N^3.
+ * Grid: N^3 voxels, x slowest, z fastest.  Fourier fields are half spectra
+ * [N][N][N/2+1] complex (interleaved re, im).  Power-spectrum bins are
+ * n_bins linear bins in |n| over (0, sqrt(3) N / 2], |n| the integer wave
+ * vector; the k = 0 mode is held at zero.
+ *
+ * Memory: every pointer named *_dev is a CUDA device pointer on the current
+ * device; every other array pointer is host memory.  The caller keeps
+ * ownership of what it passes; the library copies what it keeps.  The library
+ * owns all of its internal device buffers (allocated in bps_create and
+ * bps_set_data, released in bps_destroy).  All work is ordered on the stream
+ * given to bps_create; a call that returns host values synchronises that
+ * stream before returning.
+ *
+ * Errors: every call returns a bps_status; nothing is thrown across the ABI.
+ * After an error the context keeps the last accepted state and
+ * bps_last_error() describes the failure.
+ *
+ * Random numbers: Philox4x64-10 (Salmon et al., SC'11) with counter
+ * (element block, iteration, stage, sub) and key (seed, 0).  Each public step
+ * call draws at the context's current iteration and then advances it by one;
+ * bps_gibbs_iterate runs all stages of one iteration at one counter value.
+ */
+#ifndef BPS_H
+#define BPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bps_ctx bps_ctx;
+
+typedef enum {
+  BPS_OK = 0,
+  BPS_EINVAL = 1,    /* invalid argument, size, layout or data */
+  BPS_ENOMEM = 2,    /* device allocation failed */
+  BPS_ECUDA = 3,     /* a CUDA runtime call or kernel failed */
+  BPS_ENUMERIC = 4,  /* a non-finite energy or draw; the move was rejected */
+  BPS_ETIMEOUT = 5,  /* a bounded device wait expired */
+  BPS_ESTATE = 6     /* call out of order (e.g. a step before bps_set_data) */
+} bps_status;
+
+/* Sampler settings (Sec. 4.1.2 trajectory, Sec. 3.4 prior exponent alpha). */
+typedef struct {
+  int n_bins;              /* power-spectrum bins, 1..64 */
+  double alpha;            /* power-law prior P^-alpha (alpha = 1: Jeffreys, Sec. 3.4) */
+  int n_leapfrog;          /* leapfrog steps per HMC move */
+  double eps_max;          /* step size eps = eps_max * u, u ~ U(0,1) per move */
+  int jump;                /* 1: run the P-delta jump in bps_gibbs_iterate (Sec. 4.3) */
+  int jump_leapfrog;       /* leapfrog steps of the jump's HMC in ln P */
+  double jump_eps_max;     /* step size bound of the jump's HMC */
+  int fixed_bias_index;    /* bias held fixed (b-P degeneracy gauge); -1: none */
+  int mass_mode;           /* 0: diagonal Fourier mass of Eq. Mass_matrix;
+                              1: that mass times per-bin scales (bps_set_mass_scale) */
+  uint64_t seed;           /* Philox key */
+} bps_config;
+
+typedef struct {
+  int accepted;            /* 1 if the proposal was accepted (Eq. acceptance_rule) */
+  double dH;               /* H(proposal) - H(start), FP64 */
+  double eps;              /* step size used */
+} bps_move_info;
+
+/* Create a context for an N^3 grid of side box_len (Mpc/h) with n_sub galaxy
+ * subsamples (Sec. 2, Sec. 3.3.2).  N in {8, 16, 32, 64, 96, 128, 256};
+ * 1 <= n_sub <= 16.  cuda_stream is a cudaStream_t (NULL: the legacy default
+ * stream).  Returns BPS_EINVAL for an unsupported N, a bin layout with an empty
+ * bin, or out-of-range settings; BPS_ENOMEM if the device buffers do not fit. */
+bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* cfg,
+                      void* cuda_stream, bps_ctx** out);
+
+/* Survey data (Eq. data_model): counts_dev int32 [n_sub][N][N][N] (galaxy
+ * counts N^l_i, 0..65535) and R_dev float32 [n_sub][N][N][N] (survey response
+ * R^l_i = C^l_i F^l_i >= 0).  Copied into library buffers; the per-subsample
+ * constants sum R, sum N^2/R and N_obs (Sec. 3.6) are computed here.
+ * BPS_EINVAL if R < 0 or non-finite, a count is negative or above 65535, a
+ * voxel has R = 0 and a count > 0, or a subsample has no observed voxel. */
+bps_status bps_set_data(bps_ctx* ctx, const int32_t* counts_dev, const float* R_dev);
+
+/* Same as bps_set_data from host arrays (pageable or pinned). */
+bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R);
+
+/* Chain state (Sec. 3.2): delta_dev float32 [N][N][N] real field (its mean is
+ * dropped: the k = 0 mode is held at zero), P [n_bins], b [n_sub], nbar [n_sub]
+ * host FP64, and the iteration counter of the random streams.  P also becomes
+ * the reference spectrum of the jump's mass.  Rebuilds the local fields
+ * a = sum_l b_l^2 Nbar_l R^l and c = sum_l b_l (N^l - Nbar_l R^l)
+ * (Eq. Wiener_Posterior_force).  delta_dev may be NULL (keeps the field). */
+bps_status bps_set_state(bps_ctx* ctx, const float* delta_dev, const double* P, const double* b,
+                         const double* nbar, uint64_t iteration);
+
+/* Read the state back.  Any output pointer may be NULL. */
+bps_status bps_get_state(bps_ctx* ctx, float* delta_dev, double* P, double* b, double* nbar,
+                         uint64_t* iteration);
+
+/* Half spectrum of the current field, complex64 [N][N][N/2+1] (device). */
+bps_status bps_get_spectrum(bps_ctx* ctx, float* spec_dev);
+/* Replace the current field by a half spectrum (device); k = 0 is zeroed. */
+bps_status bps_set_spectrum(bps_ctx* ctx, const float* spec_dev);
+
+/* One HMC move of the density field (Sec. 4.1): momenta drawn afresh
+ * (p ~ N(0, M), M diagonal in Fourier space, M_k = V_cell/P_k + abar),
+ * n_leapfrog kick-drift-kick steps of size eps_max * u, Metropolis accept in
+ * FP64 (Eq. acceptance_rule).  info may be NULL (then nothing synchronises). */
+bps_status bps_hmc_step(bps_ctx* ctx, bps_move_info* info);
+
+/* Power-spectrum draw (Sec. 4.2): sigma_m = (V_cell/N^3) sum_{k in m} |delta_k|^2
+ * over the full grid, x_m ~ chi^2 with beta_m = n_m + 2 alpha - 2 degrees of
+ * freedom, P_m = sigma_m / x_m.  P_out [n_bins] and sigma_out [n_bins] (host)
+ * may be NULL. */
+bps_status bps_sample_power(bps_ctx* ctx, double* P_out, double* sigma_out);
+
+/* Bias and normalisation draws (Secs. 3.5-3.6, Apps. A-B): b_l ~ N(D/C, 1/C)
+ * with C = Nbar sum R delta^2, D = sum (N - Nbar R) delta (except the fixed
+ * index), then Nbar_l ~ GIG(1 - N_obs/2, sum R (1 + b delta)^2, sum N^2 / R),
+ * sums over R > 0; then the local fields are rebuilt.  Outputs (host, may be
+ * NULL): b_out [n_sub], nbar_out [n_sub], sums_out [n_sub][3] = (sum N delta,
+ * sum R delta, sum R delta^2). */
+bps_status bps_sample_bias_norm(bps_ctx* ctx, double* b_out, double* nbar_out, double* sums_out);
+
+/* Deterministic P-delta jump (Sec. 4.3, App. C): with u = delta/sqrt(lambda)
+ * fixed, an HMC in theta = ln P of jump_leapfrog steps targets
+ * P^-alpha x likelihood(delta(u, P)); on acceptance delta_k <- sqrt(P'/P) delta_k
+ * (Eq. det_trans).  info may be NULL. */
+bps_status bps_jump(bps_ctx* ctx, bps_move_info* info);
+
+/* n_iter full Gibbs iterations: HMC -> P -> [jump] -> b -> Nbar (Sec. 3.2).
+ * chain_out (host, may be NULL) receives per iteration n_bins P values, n_sub
+ * b, n_sub Nbar, then dH and accepted of the HMC move:
+ * n_iter * (n_bins + 2 n_sub + 2) doubles. */
+bps_status bps_gibbs_iterate(bps_ctx* ctx, int n_iter, double* chain_out);
+
+/* Per-bin multipliers s_m of the diagonal mass for mass_mode = 1 (a
+ * preconditioner choice: the mass affects efficiency, not validity,
+ * Sec. 4.1.2).  scales [n_mass_bins] host, 1 <= n_mass_bins <= 64, bins
+ * linear in |n| as for P. */
+bps_status bps_set_mass_scale(bps_ctx* ctx, int n_mass_bins, const double* scales);
+
+/* ---- building blocks of the path, for verification ---- */
+
+/* Forward 3D transform of a real field (Eq. FFT, C_hat = 1):
+ * real_dev float32 [N][N][N] -> spec_dev complex64 [N][N][N/2+1]. */
+bps_status bps_fft_r2c(bps_ctx* ctx, const float* real_dev, float* spec_dev);
+/* Inverse 3D transform (Eq. IFFT, C = 1/N^3): spec_dev -> real_dev. */
+bps_status bps_fft_c2r(bps_ctx* ctx, const float* spec_dev, float* real_dev);
+
+/* Force of the current state in Fourier space, grad_dev complex64
+ * [N][N][N/2+1]: delta_k / lambda_k + FFT(a delta - c)_k (Eq.
+ * Wiener_Posterior_force), k = 0 set to 0.  energies (host, may be NULL)
+ * receives (prior term, likelihood term) of Eq. Wiener_Posterior_psi up to a
+ * constant. */
+bps_status bps_gradient(bps_ctx* ctx, float* grad_dev, double* energies);
+
+/* n_words 64-bit Philox outputs for counter (block0 + i/4, iteration, stage,
+ * sub), word i%4, into out_dev (uint64 device array). */
+bps_status bps_philox_words(uint64_t seed, uint64_t iteration, uint64_t stage, uint64_t sub,
+                            uint64_t block0, size_t n_words, uint64_t* out_dev, void* cuda_stream);
+
+/* The momentum normals of one move: n float32 normals of stream
+ * (seed, iteration, stage 1, sub 0), element i from block i/8. */
+bps_status bps_voxel_normals(uint64_t seed, uint64_t iteration, size_t n, float* out_dev,
+                             void* cuda_stream);
+
+/* Library version string and the text of the last error of ctx (or of the
+ * last failed context-free call when ctx is NULL). */
+const char* bps_version(void);
+const char* bps_last_error(const bps_ctx* ctx);
+
+/* Number of kernels this context has launched (for launch accounting). */
+uint64_t bps_kernel_launches(const bps_ctx* ctx);
+
+void bps_destroy(bps_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPS_H */

@@ -1,0 +1,276 @@
+"""ctypes binding of the bps C ABI (include/bps.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps.  Field
+arguments are torch CUDA tensors (their device pointers are passed through);
+scalar arrays are numpy / Python sequences.  A missing or unloadable library
+raises: there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libbps.so")
+
+BPS_OK, BPS_EINVAL, BPS_ENOMEM, BPS_ECUDA, BPS_ENUMERIC, BPS_ETIMEOUT, BPS_ESTATE = range(7)
+STATUS_NAMES = ["BPS_OK", "BPS_EINVAL", "BPS_ENOMEM", "BPS_ECUDA", "BPS_ENUMERIC", "BPS_ETIMEOUT", "BPS_ESTATE"]
+
+
+class BpsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class bps_config(ctypes.Structure):
+    _fields_ = [("n_bins", ctypes.c_int), ("alpha", ctypes.c_double), ("n_leapfrog", ctypes.c_int),
+                ("eps_max", ctypes.c_double), ("jump", ctypes.c_int), ("jump_leapfrog", ctypes.c_int),
+                ("jump_eps_max", ctypes.c_double), ("fixed_bias_index", ctypes.c_int),
+                ("mass_mode", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class bps_move_info(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int), ("dH", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "bps_create": ([ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bps_config), _P,
+                    ctypes.POINTER(_P)], ctypes.c_int),
+    "bps_set_data": ([_P, _P, _P], ctypes.c_int),
+    "bps_set_data_host": ([_P, _P, _P], ctypes.c_int),
+    "bps_set_state": ([_P, _P, _D, _D, _D, ctypes.c_uint64], ctypes.c_int),
+    "bps_get_state": ([_P, _P, _D, _D, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bps_get_spectrum": ([_P, _P], ctypes.c_int),
+    "bps_set_spectrum": ([_P, _P], ctypes.c_int),
+    "bps_hmc_step": ([_P, ctypes.POINTER(bps_move_info)], ctypes.c_int),
+    "bps_sample_power": ([_P, _D, _D], ctypes.c_int),
+    "bps_sample_bias_norm": ([_P, _D, _D, _D], ctypes.c_int),
+    "bps_jump": ([_P, ctypes.POINTER(bps_move_info)], ctypes.c_int),
+    "bps_gibbs_iterate": ([_P, ctypes.c_int, _D], ctypes.c_int),
+    "bps_set_mass_scale": ([_P, ctypes.c_int, _D], ctypes.c_int),
+    "bps_fft_r2c": ([_P, _P, _P], ctypes.c_int),
+    "bps_fft_c2r": ([_P, _P, _P], ctypes.c_int),
+    "bps_gradient": ([_P, _P, _D], ctypes.c_int),
+    "bps_philox_words": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                          ctypes.c_size_t, _P, _P], ctypes.c_int),
+    "bps_voxel_normals": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.c_size_t, _P, _P], ctypes.c_int),
+    "bps_version": ([], ctypes.c_char_p),
+    "bps_last_error": ([_P], ctypes.c_char_p),
+    "bps_kernel_launches": ([_P], ctypes.c_uint64),
+    "bps_destroy": ([_P], None),
+}
+
+
+def load(path=None):
+    """Load libbps.so (built by paper_1306_1821_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise FileNotFoundError(f"{p} not found: build it with paper_1306_1821_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _darr(x, n=None):
+    if x is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if n is not None and a.size < n:
+        raise ValueError("array too short")
+    return a, a.ctypes.data_as(_D)
+
+
+def _check(ctx, status):
+    if status != BPS_OK:
+        msg = load().bps_last_error(ctx)
+        raise BpsError(status, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_config(n_bins, alpha=1.0, n_leapfrog=10, eps_max=0.3, jump=0, jump_leapfrog=10, jump_eps_max=0.05,
+                fixed_bias_index=0, mass_mode=0, seed=0):
+    return bps_config(int(n_bins), float(alpha), int(n_leapfrog), float(eps_max), int(jump), int(jump_leapfrog),
+                      float(jump_eps_max), int(fixed_bias_index), int(mass_mode), int(seed))
+
+
+def bps_create(grid_n, box_len, n_sub, cfg, stream=None):
+    lib = load()
+    ctx = _P()
+    st = lib.bps_create(int(grid_n), float(box_len), int(n_sub), ctypes.byref(cfg), _stream_ptr(stream),
+                        ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def bps_destroy(ctx):
+    load().bps_destroy(ctx)
+
+
+def bps_set_data(ctx, counts, R):
+    _check(ctx, load().bps_set_data(ctx, _dptr(counts), _dptr(R)))
+
+
+def bps_set_data_host(ctx, counts, R):
+    c = np.ascontiguousarray(counts, dtype=np.int32)
+    r = np.ascontiguousarray(R, dtype=np.float32)
+    _check(ctx, load().bps_set_data_host(ctx, c.ctypes.data_as(_P), r.ctypes.data_as(_P)))
+
+
+def bps_set_state(ctx, delta, P, b, nbar, iteration=0):
+    _, pP = _darr(P)
+    _, pb = _darr(b)
+    _, pn = _darr(nbar)
+    _check(ctx, load().bps_set_state(ctx, _dptr(delta), pP, pb, pn, int(iteration)))
+
+
+def bps_get_state(ctx, delta=None, n_bins=None, n_sub=None):
+    P = np.zeros(n_bins or 64)
+    b = np.zeros(n_sub or 16)
+    nb = np.zeros(n_sub or 16)
+    it = ctypes.c_uint64(0)
+    _check(ctx, load().bps_get_state(ctx, _dptr(delta), P.ctypes.data_as(_D), b.ctypes.data_as(_D),
+                                     nb.ctypes.data_as(_D), ctypes.byref(it)))
+    return P, b, nb, it.value
+
+
+def bps_get_spectrum(ctx, spec):
+    _check(ctx, load().bps_get_spectrum(ctx, _dptr(spec)))
+
+
+def bps_set_spectrum(ctx, spec):
+    _check(ctx, load().bps_set_spectrum(ctx, _dptr(spec)))
+
+
+def bps_hmc_step(ctx, want_info=True):
+    info = bps_move_info()
+    _check(ctx, load().bps_hmc_step(ctx, ctypes.byref(info) if want_info else None))
+    return (info.accepted, info.dH, info.eps) if want_info else None
+
+
+def bps_sample_power(ctx, n_bins, want=True):
+    if not want:
+        _check(ctx, load().bps_sample_power(ctx, None, None))
+        return None
+    P = np.zeros(n_bins)
+    s = np.zeros(n_bins)
+    _check(ctx, load().bps_sample_power(ctx, P.ctypes.data_as(_D), s.ctypes.data_as(_D)))
+    return P, s
+
+
+def bps_sample_bias_norm(ctx, n_sub, want=True):
+    if not want:
+        _check(ctx, load().bps_sample_bias_norm(ctx, None, None, None))
+        return None
+    b = np.zeros(n_sub)
+    nb = np.zeros(n_sub)
+    sums = np.zeros(3 * n_sub)
+    _check(ctx, load().bps_sample_bias_norm(ctx, b.ctypes.data_as(_D), nb.ctypes.data_as(_D),
+                                            sums.ctypes.data_as(_D)))
+    return b, nb, sums.reshape(n_sub, 3)
+
+
+def bps_jump(ctx, want_info=True):
+    info = bps_move_info()
+    _check(ctx, load().bps_jump(ctx, ctypes.byref(info) if want_info else None))
+    return (info.accepted, info.dH, info.eps) if want_info else None
+
+
+def bps_gibbs_iterate(ctx, n_iter, rec_len=None):
+    if rec_len is None:
+        _check(ctx, load().bps_gibbs_iterate(ctx, int(n_iter), None))
+        return None
+    out = np.zeros(int(n_iter) * rec_len)
+    _check(ctx, load().bps_gibbs_iterate(ctx, int(n_iter), out.ctypes.data_as(_D)))
+    return out.reshape(int(n_iter), rec_len)
+
+
+def bps_set_mass_scale(ctx, scales):
+    a, p = _darr(scales)
+    _check(ctx, load().bps_set_mass_scale(ctx, int(a.size), p))
+
+
+def bps_fft_r2c(ctx, real, spec):
+    _check(ctx, load().bps_fft_r2c(ctx, _dptr(real), _dptr(spec)))
+
+
+def bps_fft_c2r(ctx, spec, real):
+    _check(ctx, load().bps_fft_c2r(ctx, _dptr(spec), _dptr(real)))
+
+
+def bps_gradient(ctx, grad):
+    e = np.zeros(2)
+    _check(ctx, load().bps_gradient(ctx, _dptr(grad), e.ctypes.data_as(_D)))
+    return e
+
+
+def bps_philox_words(seed, iteration, stage, sub, block0, out, stream=None):
+    _check(None, load().bps_philox_words(int(seed), int(iteration), int(stage), int(sub), int(block0),
+                                         int(out.numel()), _dptr(out), _stream_ptr(stream)))
+
+
+def bps_voxel_normals(seed, iteration, out, stream=None):
+    _check(None, load().bps_voxel_normals(int(seed), int(iteration), int(out.numel()), _dptr(out),
+                                          _stream_ptr(stream)))
+
+
+def bps_version():
+    return load().bps_version().decode()
+
+
+def bps_kernel_launches(ctx):
+    return int(load().bps_kernel_launches(ctx))
+
+
+class Sampler:
+    """One chain of the sampler on the current CUDA device (owns a bps context)."""
+
+    def __init__(self, N, box, n_sub, n_bins, stream=None, **cfg):
+        self.N, self.box, self.n_sub, self.n_bins = int(N), float(box), int(n_sub), int(n_bins)
+        self.cfg = make_config(n_bins, **cfg)
+        self.ctx = bps_create(N, box, n_sub, self.cfg, stream)
+
+    @property
+    def rec_len(self):
+        return self.n_bins + 2 * self.n_sub + 2
+
+    def close(self):
+        if self.ctx is not None:
+            bps_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,391 @@
+// Scalar stages of the multiple-block scan, run on the device so that a Gibbs
+// iteration needs no host round trip: step size and Metropolis decisions of the
+// HMC moves (Sec. 4.1, Eq. acceptance_rule), the chi^2 draw of the power
+// spectrum (Sec. 4.2), the normal bias draw (Sec. 3.5, App. B), the GIG draw of
+// the normalisations (Sec. 3.6, App. A) and the HMC in ln P of the jump
+// (Sec. 4.3, App. C).  All decisions are taken in FP64 from Philox4x64-10
+// words at fixed counters.
+#include <math.h>
+
+#include "bps_internal.h"
+#include "bps_passes.cuh"
+
+namespace bps {
+
+constexpr int MAX_ATTEMPTS = 64;
+
+// Deterministic sum of n partials (stride 1) by one block of 256 threads;
+// the value is valid in thread 0.
+__device__ double sum_partials(const double* p, int n, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) v += p[i];
+  return block_sum<256>(v, sh);
+}
+
+// ------------------------------------------------------------------ HMC move
+__global__ void k_move_begin(ScalarArgs a) {
+  DevState* ds = a.ds;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    P4 r = philox(0, ds->iteration, ST_HMC, 0, a.seed);
+    ds->eps = a.eps_max * u52(r.w[0]);
+    ds->u_acc = u52(r.w[1]);
+  }
+  if (t < MAXB) {
+    if (t < a.n_bins) {
+      // lambda_m = P_m / V_cell (Eq. dens_prior in Fourier space); M = 1/lambda + abar (Eq. Mass_matrix)
+      const double il = a.Vc / ds->P[t];
+      const double M = il + ds->abar;
+      ds->inv_lambda[t] = (float)il;
+      ds->inv_M[t] = (float)(1.0 / M);
+      ds->sqrt_M[t] = (float)sqrt(M);
+    } else {
+      ds->inv_lambda[t] = 0.f;
+      ds->inv_M[t] = 0.f;
+      ds->sqrt_M[t] = 0.f;
+    }
+    const double sc = t < a.n_mass ? ds->mass_scale[t] : 1.0;
+    ds->inv_ms[t] = (float)(1.0 / sc);
+    ds->sqrt_ms[t] = (float)sqrt(sc);
+  }
+}
+
+// H = (1/2N^3) sum w (|p|^2/M + |delta|^2/lambda) + (1/2) sum (a delta^2 - 2 c delta)
+__global__ void k_move_end(ScalarArgs a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz) {
+  __shared__ double sh[32];
+  DevState* ds = a.ds;
+  const double h = 0.5 * a.inv_nv;
+  const double K0 = sum_partials(a.part + r_init, nx, sh) * h;
+  const double E0 = sum_partials(a.part + r_init + a.stride, nx, sh) * h;
+  const double L0 = sum_partials(a.part + r_lik0, nz, sh);
+  const double K1 = sum_partials(a.part + r_final, nx, sh) * h;
+  const double E1 = sum_partials(a.part + r_final + a.stride, nx, sh) * h;
+  const double L1 = sum_partials(a.part + r_lik1, nz, sh);
+  if (threadIdx.x == 0) {
+    const double H0 = K0 + E0 + L0, H1 = K1 + E1 + L1;
+    const double dH = H1 - H0;
+    ds->H0 = H0;
+    ds->H1 = H1;
+    ds->dH = dH;
+    ds->lik0 = L0;
+    ds->lik1 = L1;
+    int acc = 0;
+    if (!isfinite(dH)) {
+      ds->status |= ST_NONFINITE;
+    } else {
+      acc = log(ds->u_acc) < -dH;   // Eq. acceptance_rule, FP64
+    }
+    ds->accepted = acc;
+    if (acc) {
+      ds->cur = 1 - ds->cur;
+      ds->n_accepted += 1;
+    }
+    ds->n_moves += 1;
+  }
+}
+
+// ------------------------------------------------------------------ P draw
+// Gamma(shape) by Marsaglia & Tsang (ACM TOMS 2000); attempt j of bin m reads
+// Philox block (m, iteration, ST_POWER, j): words 0,1 -> normal, word 2 -> uniform;
+// shape < 1 uses Gamma(shape + 1) U^(1/shape) with U from word 3 of attempt 0.
+__device__ double gamma_mt(double shape, uint64_t seed, uint64_t it, int m, int* fail) {
+  const bool boost = shape < 1.0;
+  const double aa = boost ? shape + 1.0 : shape;
+  const double d = aa - 1.0 / 3.0;
+  const double c = 1.0 / sqrt(9.0 * d);
+  double val = d;
+  bool ok = false;
+  for (int j = 0; j < MAX_ATTEMPTS && !ok; ++j) {
+    P4 r = philox((uint64_t)m, it, ST_POWER, (uint64_t)j, seed);
+    const double z = normal64(r.w[0], r.w[1]);
+    const double t = 1.0 + c * z;
+    if (t <= 0.0) continue;
+    const double v = t * t * t;
+    const double u = u52(r.w[2]);
+    if (log(u) < 0.5 * z * z + d - d * v + d * log(v)) {
+      val = d * v;
+      ok = true;
+    }
+  }
+  if (!ok) *fail = 1;
+  if (boost) {
+    P4 r = philox((uint64_t)m, it, ST_POWER, 0, seed);
+    val *= exp(log(u52(r.w[3])) / shape);
+  }
+  return val;
+}
+
+// block m: sigma_m = (V_cell/N^3) sum_{k in m} w |delta_k|^2; then (draw) P_m = sigma_m / x,
+// x ~ chi^2_beta = 2 Gamma(beta/2), beta = n_m + 2 alpha - 2 (Sec. 4.2, Eq. XI_SQUARE)
+__global__ void k_power(ScalarArgs a, int region, int nx, int draw) {
+  __shared__ double sh[32];
+  DevState* ds = a.ds;
+  const int m = blockIdx.x;
+  const double s = sum_partials(a.part + region + (size_t)m * a.stride, nx, sh);
+  if (threadIdx.x == 0) {
+    const double sigma = s * a.Vc * a.inv_nv;
+    ds->sigma[m] = sigma;
+    if (draw) {
+      const double beta = ds->nmodes[m] + 2.0 * a.alpha - 2.0;
+      int fail = 0;
+      const double g = gamma_mt(0.5 * beta, a.seed, ds->iteration, m, &fail);
+      if (fail || !(sigma > 0.0)) atomicOr(&ds->status, ST_DRAW_FAIL);
+      else ds->P[m] = sigma / (2.0 * g);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ GIG draw
+// Density ~ x^(p-1) exp(-(A x + B/x)/2) (Eq. GIG_post).  With eta = sqrt(B/A),
+// omega = sqrt(A B), y = x/eta (p >= 0) or eta/x (p < 0) has density
+// h(y) ~ y^(lam-1) exp(-omega (y + 1/y)/2), lam = |p|; sampled by the
+// ratio-of-uniforms method with mode shift (Kinderman & Monahan 1977), the
+// bounding rectangle found by bisection, everything in log space about the mode.
+__device__ double gig_logh(double y, double lam, double om, double m) {
+  return (lam - 1.0) * log1p((y - m) / m) - 0.5 * om * (y - m) * (1.0 - 1.0 / (y * m));
+}
+__device__ double gig_dphi(double y, double lam, double om, double m) {
+  return 1.0 / (y - m) + 0.5 * ((lam - 1.0) / y - 0.5 * om + 0.5 * om / (y * y));
+}
+
+__device__ double gig_draw(double p, double A, double B, uint64_t seed, uint64_t it, int l, int* fail) {
+  const double lam = fabs(p);
+  const double om = sqrt(A * B);
+  const double eta = sqrt(B / A);
+  const double q = lam - 1.0;
+  const double sq = sqrt(q * q + om * om);
+  const double m = q >= 0.0 ? (q + sq) / om : om / (sq - q);
+  // upper extreme of (y - m) sqrt(h(y)/h(m))
+  double step = m, hi = m + step;
+  for (int i = 0; i < 200 && gig_dphi(hi, lam, om, m) > 0.0; ++i) {
+    step *= 2.0;
+    hi = m + step;
+  }
+  double lo = m;
+  for (int i = 0; i < 200; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (gig_dphi(mid, lam, om, m) > 0.0) lo = mid;
+    else hi = mid;
+  }
+  const double yp = 0.5 * (lo + hi);
+  const double vp = (yp - m) * exp(0.5 * gig_logh(yp, lam, om, m));
+  lo = 0.0;
+  hi = m;
+  for (int i = 0; i < 200; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (gig_dphi(mid, lam, om, m) < 0.0) hi = mid;
+    else lo = mid;
+  }
+  const double ym = 0.5 * (lo + hi);
+  const double vm = ym > 0.0 ? (ym - m) * exp(0.5 * gig_logh(ym, lam, om, m)) : -m;
+  double y = m;
+  bool ok = false;
+  for (int j = 0; j < MAX_ATTEMPTS && !ok; ++j) {
+    P4 r = philox((uint64_t)l, it, ST_NBAR, (uint64_t)j, seed);
+    const double u = u52(r.w[0]);
+    const double v = vm + (vp - vm) * u52(r.w[1]);
+    const double yy = v / u + m;
+    if (yy <= 0.0) continue;
+    if (2.0 * log(u) <= gig_logh(yy, lam, om, m)) {
+      y = yy;
+      ok = true;
+    }
+  }
+  if (!ok) *fail = 1;
+  return p >= 0.0 ? eta * y : eta / y;
+}
+
+// block l: S1 = sum N delta, S2 = sum R delta, S3 = sum R delta^2; then
+// b_l ~ N(D/C, 1/C), C = Nbar S3, D = S1 - Nbar S2 (Sec. 3.5, App. B; skipped for
+// the fixed index) and Nbar_l ~ GIG(1 - N_obs/2, sum R + 2 b S2 + b^2 S3, sum N^2/R)
+__global__ void k_bias_nbar(ScalarArgs a, int region, int nz) {
+  __shared__ double sh[32];
+  DevState* ds = a.ds;
+  const int l = blockIdx.x;
+  double S[3];
+  for (int q = 0; q < 3; ++q) S[q] = sum_partials(a.part + region + (size_t)(3 * l + q) * a.stride, nz, sh);
+  if (threadIdx.x == 0) {
+    const uint64_t it = ds->iteration;
+    ds->sums[l][0] = S[0];
+    ds->sums[l][1] = S[1];
+    ds->sums[l][2] = S[2];
+    double b = ds->b[l];
+    const double nb = ds->nbar[l];
+    int fail = 0;
+    if (l != a.fixed_bias) {
+      const double C = nb * S[2];
+      const double D = S[0] - nb * S[1];
+      P4 r = philox((uint64_t)l, it, ST_BIAS, 0, a.seed);
+      const double z = normal64(r.w[0], r.w[1]);
+      if (C > 0.0) b = D / C + z / sqrt(C);
+      else fail = 1;
+    }
+    const double A = ds->sumR[l] + 2.0 * b * S[1] + b * b * S[2];
+    const double p = 1.0 - 0.5 * ds->nobs[l];
+    double x = nb;
+    if (A > 0.0 && ds->sumB[l] > 0.0) x = gig_draw(p, A, ds->sumB[l], a.seed, it, l, &fail);
+    else fail = 1;
+    if (fail || !isfinite(b) || !isfinite(x)) {
+      atomicOr(&ds->status, ST_DRAW_FAIL);
+    } else {
+      ds->b[l] = b;
+      ds->nbar[l] = x;
+    }
+  }
+}
+
+__global__ void k_abar(ScalarArgs a, int region, int nblk) {
+  __shared__ double sh[32];
+  const double s = sum_partials(a.part + region, nblk, sh);
+  if (threadIdx.x == 0) a.ds->abar = s * a.inv_nv;
+}
+
+// ------------------------------------------------------------------ jump move
+// HMC in theta = ln P with the whitened field fixed (Sec. 4.3, App. C).
+// Mass mu_m = max(1, abar P_ref_m sigma_m / (4 V_cell P_m)): built from the
+// whitened field and a fixed reference spectrum, never from the current P.
+__global__ void k_jump_begin(ScalarArgs a) {
+  DevState* ds = a.ds;
+  const int m = threadIdx.x;
+  const uint64_t it = ds->iteration;
+  if (m == 0) {
+    P4 r = philox(0, it, ST_JUMP, 0, a.seed);
+    ds->jeps = a.jeps_max * u52(r.w[0]);
+    ds->ju_acc = u52(r.w[1]);
+    ds->jaccepted = 0;
+  }
+  if (m < MAXB) {
+    if (m < a.n_bins) {
+      const double mu = fmax(1.0, ds->abar * ds->P_ref[m] * ds->sigma[m] / (4.0 * a.Vc * ds->P[m]));
+      P4 r = philox((uint64_t)m, it, ST_JUMP_MOM, 0, a.seed);
+      ds->mu[m] = mu;
+      ds->rho[m] = sqrt(mu) * normal64(r.w[0], r.w[1]);
+      ds->th[m] = log(ds->P[m]);
+    }
+    ds->js[m] = 1.f;
+  }
+}
+
+// blocks m < n_bins: gradient d psi_J / d theta_m = (alpha - 1) + (1/2N^3) sum_{k in m} w Re(conj(g) delta);
+// block n_bins: likelihood energy at theta
+__global__ void k_jump_reduce(ScalarArgs a, int r_grad, int nx, int r_lik, int nz) {
+  __shared__ double sh[32];
+  DevState* ds = a.ds;
+  const int m = blockIdx.x;
+  if (m < a.n_bins) {
+    const double s = sum_partials(a.part + r_grad + (size_t)m * a.stride, nx, sh);
+    if (threadIdx.x == 0) ds->jgrad[m] = (a.alpha - 1.0) + 0.5 * a.inv_nv * s;
+  } else {
+    const double s = sum_partials(a.part + r_lik, nz, sh);
+    if (threadIdx.x == 0) ds->jlik = s;
+  }
+}
+
+__global__ void k_jump_update(ScalarArgs a, int kind) {
+  __shared__ double sh[32];
+  DevState* ds = a.ds;
+  const int m = threadIdx.x;   // 64 threads
+  const double eps = ds->jeps;
+  const bool act = m < a.n_bins;
+  double kin = 0.0, pri = 0.0;
+  double rho = act ? ds->rho[m] : 0.0, th = act ? ds->th[m] : 0.0;
+  const double mu = act ? ds->mu[m] : 1.0, g = act ? ds->jgrad[m] : 0.0;
+  if (kind == J_FIRST && act) {
+    kin = 0.5 * rho * rho / mu;
+    pri = (a.alpha - 1.0) * th;
+  }
+  if (act) {
+    const double ek = (kind == J_MID) ? eps : 0.5 * eps;
+    rho -= ek * g;
+    if (kind != J_LAST) th += eps * rho / mu;
+  }
+  if (kind == J_LAST && act) {
+    kin = 0.5 * rho * rho / mu;
+    pri = (a.alpha - 1.0) * th;
+  }
+  // 64-thread sums (two warps)
+  double e = kin + pri;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  if ((m & 31) == 0) sh[m >> 5] = e;
+  __syncthreads();
+  const double E = sh[0] + sh[1];
+  if (act) {
+    ds->rho[m] = rho;
+    ds->th[m] = th;
+    ds->js[m] = (float)sqrt(exp(th) / ds->P[m]);
+  }
+  if (kind == J_FIRST && m == 0) ds->jH0 = E + ds->jlik;
+  if (kind == J_LAST) {
+    __shared__ int s_acc;
+    if (m == 0) {
+      const double H1 = E + ds->jlik;
+      const double dH = H1 - ds->jH0;
+      ds->jH1 = H1;
+      ds->jdH = dH;
+      int acc = 0;
+      if (!isfinite(dH)) ds->status |= ST_NONFINITE;
+      else acc = log(ds->ju_acc) < -dH;
+      ds->jaccepted = acc;
+      s_acc = acc;
+    }
+    __syncthreads();
+    if (act && s_acc) ds->P[m] = exp(th);
+  }
+}
+
+// ------------------------------------------------------------------ misc
+__global__ void k_reduce_to(ScalarArgs a, int region, int nblk, double scale, double* out) {
+  __shared__ double sh[32];
+  const int q = blockIdx.x;
+  const double s = sum_partials(a.part + region + (size_t)q * a.stride, nblk, sh);
+  if (threadIdx.x == 0) out[q] = s * scale;
+}
+
+// chain record: P[n_bins], b[n_sub], nbar[n_sub], dH, accepted
+__global__ void k_record(ScalarArgs a, double* rec) {
+  DevState* ds = a.ds;
+  const int t = threadIdx.x;
+  if (t < a.n_bins) rec[t] = ds->P[t];
+  if (t < a.n_sub) {
+    rec[a.n_bins + t] = ds->b[t];
+    rec[a.n_bins + a.n_sub + t] = ds->nbar[t];
+  }
+  if (t == 0) {
+    rec[a.n_bins + 2 * a.n_sub] = ds->dH;
+    rec[a.n_bins + 2 * a.n_sub + 1] = (double)ds->accepted;
+  }
+}
+
+__global__ void k_advance(DevState* ds) { ds->iteration += 1; }
+
+__global__ void k_zero_dc(float2* spec) { spec[0] = make_float2(0.f, 0.f); }
+
+void launch_move_begin(const ScalarArgs& a, cudaStream_t s) { k_move_begin<<<1, MAXB, 0, s>>>(a); }
+void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz,
+                     cudaStream_t s) {
+  k_move_end<<<1, 256, 0, s>>>(a, r_init, r_lik0, r_final, r_lik1, nx, nz);
+}
+void launch_power(const ScalarArgs& a, int region, int nx, int draw, cudaStream_t s) {
+  k_power<<<a.n_bins, 256, 0, s>>>(a, region, nx, draw);
+}
+void launch_bias_nbar(const ScalarArgs& a, int region, int nz, cudaStream_t s) {
+  k_bias_nbar<<<a.n_sub, 256, 0, s>>>(a, region, nz);
+}
+void launch_abar(const ScalarArgs& a, int region, int nblk, cudaStream_t s) { k_abar<<<1, 256, 0, s>>>(a, region, nblk); }
+void launch_jump_begin(const ScalarArgs& a, cudaStream_t s) { k_jump_begin<<<1, MAXB, 0, s>>>(a); }
+void launch_jump_reduce(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, cudaStream_t s) {
+  k_jump_reduce<<<a.n_bins + 1, 256, 0, s>>>(a, r_grad, nx, r_lik, nz);
+}
+void launch_jump_update(const ScalarArgs& a, int kind, cudaStream_t s) { k_jump_update<<<1, MAXB, 0, s>>>(a, kind); }
+void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, double scale, double* out_dev,
+                      cudaStream_t s) {
+  k_reduce_to<<<count, 256, 0, s>>>(a, region, nblk, scale, out_dev);
+}
+void launch_record(const ScalarArgs& a, double* rec_dev, cudaStream_t s) { k_record<<<1, MAXB, 0, s>>>(a, rec_dev); }
+void launch_advance(DevState* ds, cudaStream_t s) { k_advance<<<1, 1, 0, s>>>(ds); }
+void launch_zero_dc(float2* spec, cudaStream_t s) { k_zero_dc<<<1, 1, 0, s>>>(spec); }
+
+}  // namespace bps

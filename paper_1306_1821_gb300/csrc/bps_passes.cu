@@ -1,0 +1,733 @@
+// Field-pass kernels of the sampler and their per-grid launch tables.
+//
+// HMC leapfrog step (Sec. 4.1.2, Eqs. HAMILTON1_a / HAMILTON2_a, kick-drift-kick)
+// in four passes, each one HBM round trip of the half spectra it touches:
+//   x pass  : ghat = FFT_x(W); p -= eps_k (delta/lambda + ghat); delta += eps p / M;
+//             W = IFFT_x(delta)                         (reads W, delta, p; writes all three)
+//   y pass  : W = IFFT_y(W)
+//   z pass  : delta = C2R_z(W) / N^3; g = a delta - c; W = R2C_z(g)   (reads a, c)
+//   y pass  : W = FFT_y(W)
+// so the force of Eq. Wiener_Posterior_force costs one 3D C2R and one 3D R2C
+// with the prior and the voxel-local likelihood fused into the passes.
+#include "bps_passes.cuh"
+#include "bps_internal.h"
+
+namespace bps {
+
+enum XMode {
+  X_INIT = 0,   // momentum: p = sqrt(M) FFT_x(p); energies of p and delta; W = IFFT_x(delta)
+  X_LEAP,       // kick (previous force) + drift + inverse x of the new delta
+  X_FINAL,      // last half kick; kinetic and prior energies of the end point
+  X_INV,        // dst = IFFT_x(src)
+  X_FWD,        // dst = FFT_x(src)
+  X_GRAD,       // dst = delta/lambda + FFT_x(W); prior energy
+  X_JINV,       // W = IFFT_x(js_m delta)                (jump: field at theta)
+  X_JGRAD,      // per-bin sum w Re(conj(FFT_x(W)) js_m delta)
+  X_SCALE,      // delta *= js_m if the jump was accepted
+  X_BINPOW      // per-bin sum w |delta|^2
+};
+
+enum ZMode { Z_GRAD = 0, Z_NOISE, Z_R2C, Z_C2R, Z_SUMS };
+
+// state buffer i without indexing the parameter array at run time
+__device__ __forceinline__ float2* dsel(const Fields& fp, int i) { return i ? fp.dh[1] : fp.dh[0]; }
+
+struct XArgs {
+  const float2* src;
+  float2* dst;
+  int first;
+  int region;    // offset (doubles) of this launch's partial sums in Fields::part
+};
+
+struct ZArgs {
+  const float2* src;
+  float2* dst;
+  const float* rin;
+  float* rout;
+  int region;
+  uint64_t seed;
+};
+
+// ------------------------------------------------------------------ x pass
+template <int N, int MODE>
+__global__ void __launch_bounds__(Cfg<N>::NT, 2) k_xpass(Fields fp, XArgs xa) {
+  using C = Cfg<N>;
+  constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT, NW = NT / 32;
+  constexpr bool BINNED = (MODE == X_JGRAD || MODE == X_BINPOW);
+  __shared__ float2 s_tw[N];
+  __shared__ __align__(16) float2 s_ex[N * F];
+  __shared__ int s_thr[MAXB], s_mthr[MAXB];
+  __shared__ float s_il[MAXB], s_im[MAXB], s_sm[MAXB], s_ims[MAXB], s_sms[MAXB], s_js[MAXB];
+  __shared__ double s_red[32];
+  __shared__ double s_wb[BINNED ? NW : 1][MAXB];
+
+  const int t = threadIdx.x;
+  DevState* ds = fp.ds;
+  if constexpr (MODE == X_SCALE) {
+    if (!ds->jaccepted) return;   // uniform across the grid
+  }
+  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
+  for (int i = t; i < MAXB; i += NT) {
+    s_thr[i] = ds->thr[i];
+    s_mthr[i] = ds->mthr[i];
+    s_il[i] = ds->inv_lambda[i];
+    s_im[i] = ds->inv_M[i];
+    s_sm[i] = ds->sqrt_M[i];
+    s_ims[i] = ds->inv_ms[i];
+    s_sms[i] = ds->sqrt_ms[i];
+    s_js[i] = ds->js[i];
+    if constexpr (BINNED) {
+      for (int w = 0; w < NW; ++w) s_wb[w][i] = 0.0;
+    }
+  }
+  __syncthreads();
+
+  const Tile<N> T = tile_x<N>(blockIdx.x);
+  const int f = t % F;
+  const int ja = t / F;                       // row group of the spatial (x-) layout
+  const int ky = T.ky0 + f * T.dky, kz = T.kz0 + f * T.dkz;
+  const int ny = sgn_n<N>(ky);
+  const int n2yz = ny * ny + kz * kz;
+  const float wk = (kz == 0 || kz == C::H) ? 1.f : 2.f;
+  const long long colo = T.base + (long long)f * T.cs;
+  const int cur = ds->cur;
+  const bool mm = fp.mass_mode != 0;
+
+  float2 v[C::RMAX];
+  auto mode_bin = [&](int k, float& il, float& im, float& sm) -> int {
+    const int nx = sgn_n<N>(k);
+    const int n2 = nx * nx + n2yz;
+    const int m = bin_of(n2, s_thr);
+    if (m >= 0) {
+      il = s_il[m];
+      im = s_im[m];
+      sm = s_sm[m];
+      if (mm) {
+        const int j = bin_of(n2, s_mthr);
+        im *= s_ims[j];
+        sm *= s_sms[j];
+      }
+    } else {
+      il = im = sm = 0.f;
+    }
+    return m;
+  };
+
+  // ---------------- modes that start from a spatial-x tile: forward transform
+  if constexpr (MODE == X_INIT || MODE == X_LEAP || MODE == X_FINAL || MODE == X_FWD || MODE == X_GRAD ||
+                MODE == X_JGRAD) {
+    const float2* in = (MODE == X_INIT) ? fp.ph : (MODE == X_FWD) ? xa.src : fp.W;
+    // X_FWD with no destination writes the current state buffer
+    if (ja < R1) {
+#pragma unroll
+      for (int b = 0; b < R2; ++b) v[b] = in[colo + (long long)(ja + R1 * b) * T.rs];
+    }
+    fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
+  }
+  const int jc = t / F;                       // row group of the Fourier (kx-) layout
+  const bool act = jc < R2;
+
+  if constexpr (MODE == X_FWD) {
+    if (act) {
+      float2* out = xa.dst ? xa.dst : dsel(fp, cur);
+#pragma unroll
+      for (int d = 0; d < R1; ++d) out[colo + (long long)(jc + R2 * d) * T.rs] = v[d];
+    }
+    return;
+  }
+
+  if constexpr (MODE == X_INIT) {
+    // momentum p = sqrt(M_k) FFT(xi); kinetic energy (1/2N^3) sum w |p|^2 / M
+    float eK = 0.f, eP = 0.f;
+    float2 x[R1];
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) x[d] = dsel(fp, cur)[colo + (long long)(jc + R2 * d) * T.rs];
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const int k = jc + R2 * d;
+        float il, im, sm;
+        const int m = mode_bin(k, il, im, sm);
+        float2 p = m >= 0 ? cscale(v[d], sm) : make_float2(0.f, 0.f);
+        fp.ph[colo + (long long)k * T.rs] = p;
+        eK += wk * (p.x * p.x + p.y * p.y) * im;
+        float2 xx = m >= 0 ? x[d] : make_float2(0.f, 0.f);
+        eP += wk * (xx.x * xx.x + xx.y * xx.y) * il;
+        v[d] = xx;
+      }
+    }
+    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    if (ja < R1) {
+#pragma unroll
+      for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
+    }
+    double sK = block_sum<NT>((double)eK, s_red);
+    double sP = block_sum<NT>((double)eP, s_red);
+    if (t == 0) {
+      fp.part[xa.region + blockIdx.x] = sK;
+      fp.part[xa.region + fp.part_stride + blockIdx.x] = sP;
+    }
+    return;
+  }
+
+  if constexpr (MODE == X_LEAP) {
+    const float2* src = xa.first ? dsel(fp, cur) : dsel(fp, 1 - cur);
+    float2* dst = dsel(fp, 1 - cur);
+    const float eps = (float)ds->eps;
+    const float ek = xa.first ? 0.5f * eps : eps;
+    float2 x[R1], p[R1];
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const long long idx = colo + (long long)(jc + R2 * d) * T.rs;
+        x[d] = src[idx];
+        p[d] = fp.ph[idx];
+      }
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const int k = jc + R2 * d;
+        float il, im, sm;
+        const int m = mode_bin(k, il, im, sm);
+        float2 xx = x[d], pp = p[d];
+        if (m >= 0) {
+          const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
+          pp.x = fmaf(-ek, gx, pp.x);
+          pp.y = fmaf(-ek, gy, pp.y);
+          const float s = eps * im;
+          xx.x = fmaf(s, pp.x, xx.x);
+          xx.y = fmaf(s, pp.y, xx.y);
+        } else {
+          xx = make_float2(0.f, 0.f);
+          pp = make_float2(0.f, 0.f);
+        }
+        const long long idx = colo + (long long)k * T.rs;
+        fp.ph[idx] = pp;
+        dst[idx] = xx;
+        v[d] = xx;
+      }
+    }
+    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    if (ja < R1) {
+#pragma unroll
+      for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
+    }
+    return;
+  }
+
+  if constexpr (MODE == X_FINAL) {
+    const float2* src = dsel(fp, 1 - cur);
+    const float eps = (float)ds->eps;
+    const float ek = 0.5f * eps;
+    float eK = 0.f, eP = 0.f;
+    float2 x[R1], p[R1];
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const long long idx = colo + (long long)(jc + R2 * d) * T.rs;
+        x[d] = src[idx];
+        p[d] = fp.ph[idx];
+      }
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const int k = jc + R2 * d;
+        float il, im, sm;
+        const int m = mode_bin(k, il, im, sm);
+        if (m >= 0) {
+          float2 xx = x[d], pp = p[d];
+          const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
+          pp.x = fmaf(-ek, gx, pp.x);
+          pp.y = fmaf(-ek, gy, pp.y);
+          eK += wk * (pp.x * pp.x + pp.y * pp.y) * im;
+          eP += wk * (xx.x * xx.x + xx.y * xx.y) * il;
+        }
+      }
+    }
+    double sK = block_sum<NT>((double)eK, s_red);
+    double sP = block_sum<NT>((double)eP, s_red);
+    if (t == 0) {
+      fp.part[xa.region + blockIdx.x] = sK;
+      fp.part[xa.region + fp.part_stride + blockIdx.x] = sP;
+    }
+    return;
+  }
+
+  if constexpr (MODE == X_GRAD) {
+    float eP = 0.f;
+    if (act) {
+      float2 x[R1];
+#pragma unroll
+      for (int d = 0; d < R1; ++d) x[d] = dsel(fp, cur)[colo + (long long)(jc + R2 * d) * T.rs];
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const int k = jc + R2 * d;
+        float il, im, sm;
+        const int m = mode_bin(k, il, im, sm);
+        float2 g = make_float2(0.f, 0.f);
+        if (m >= 0) {
+          g = make_float2(fmaf(x[d].x, il, v[d].x), fmaf(x[d].y, il, v[d].y));
+          eP += wk * (x[d].x * x[d].x + x[d].y * x[d].y) * il;
+        }
+        xa.dst[colo + (long long)k * T.rs] = g;
+      }
+    }
+    double sP = block_sum<NT>((double)eP, s_red);
+    if (t == 0) fp.part[xa.region + blockIdx.x] = sP;
+    return;
+  }
+
+  if constexpr (MODE == X_INV || MODE == X_JINV) {
+    // X_INV with no source reads the current state buffer
+    const float2* src = (MODE == X_INV && xa.src) ? xa.src : dsel(fp, cur);
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) v[d] = src[colo + (long long)(jc + R2 * d) * T.rs];
+      if constexpr (MODE == X_JINV) {
+#pragma unroll
+        for (int d = 0; d < R1; ++d) {
+          const int k = jc + R2 * d;
+          const int nx = sgn_n<N>(k);
+          const int m = bin_of(nx * nx + n2yz, s_thr);
+          v[d] = m >= 0 ? cscale(v[d], s_js[m]) : make_float2(0.f, 0.f);
+        }
+      }
+    }
+    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    float2* out = (MODE == X_INV) ? xa.dst : fp.W;
+    if (ja < R1) {
+#pragma unroll
+      for (int b = 0; b < R2; ++b) out[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
+    }
+    return;
+  }
+
+  if constexpr (MODE == X_SCALE) {
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const int k = jc + R2 * d;
+        const int nx = sgn_n<N>(k);
+        const int m = bin_of(nx * nx + n2yz, s_thr);
+        const long long idx = colo + (long long)k * T.rs;
+        dsel(fp, cur)[idx] = m >= 0 ? cscale(dsel(fp, cur)[idx], s_js[m]) : make_float2(0.f, 0.f);
+      }
+    }
+    return;
+  }
+
+  if constexpr (BINNED) {
+    const int warp = t >> 5;
+#pragma unroll
+    for (int d = 0; d < R1; ++d) {
+      float e = 0.f;
+      int m = -1;
+      if (act) {
+        const int k = jc + R2 * d;
+        const int nx = sgn_n<N>(k);
+        m = bin_of(nx * nx + n2yz, s_thr);
+        float2 x = dsel(fp, cur)[colo + (long long)k * T.rs];
+        if (m >= 0) {
+          if constexpr (MODE == X_BINPOW) {
+            e = wk * (x.x * x.x + x.y * x.y);
+          } else {
+            const float s = s_js[m];
+            e = wk * s * (v[d].x * x.x + v[d].y * x.y);
+          }
+        }
+      }
+      bin_accumulate<F>(e, m, s_wb[warp]);
+    }
+    __syncthreads();
+    for (int m = t; m < MAXB; m += NT) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s += s_wb[w][m];
+      fp.part[xa.region + m * fp.part_stride + blockIdx.x] = s;
+    }
+    return;
+  }
+}
+
+// ------------------------------------------------------------------ y pass
+template <int N, int DIR>
+__global__ void __launch_bounds__(Cfg<N>::NT) k_ypass(Fields fp, float2* buf) {
+  using C = Cfg<N>;
+  constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT;
+  __shared__ float2 s_tw[N];
+  __shared__ __align__(16) float2 s_ex[N * F];
+  const int t = threadIdx.x;
+  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
+  __syncthreads();
+  const Tile<N> T = tile_y<N>(blockIdx.x);
+  const int f = t % F, j = t / F;
+  const long long colo = T.base + (long long)f * T.cs;
+  float2 v[C::RMAX];
+  if constexpr (DIR == FWD) {
+    if (j < R1) {
+#pragma unroll
+      for (int b = 0; b < R2; ++b) v[b] = buf[colo + (long long)(j + R1 * b) * T.rs];
+    }
+    fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
+    if (j < R2) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) buf[colo + (long long)(j + R2 * d) * T.rs] = v[d];
+    }
+  } else {
+    if (j < R2) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) v[d] = buf[colo + (long long)(j + R2 * d) * T.rs];
+    }
+    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    if (j < R1) {
+#pragma unroll
+      for (int b = 0; b < R2; ++b) buf[colo + (long long)(j + R1 * b) * T.rs] = v[b];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ z pass
+// 16 pairs of consecutive z lines per tile; line 2f is the real part and line
+// 2f+1 the imaginary part of one complex transform of length N.
+template <int N, int MODE>
+__global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
+  using C = Cfg<N>;
+  constexpr int R1 = C::R1, R2 = C::R2, H = C::H, ZP = C::ZP, NTZ = C::NTZ;
+  constexpr int LINES = 2 * C::LP;
+  constexpr int BUF = 16 * (N + C::RMAX);
+  static_assert(BUF >= LINES * ZP, "staging does not fit");
+  __shared__ float2 s_tw[N];
+  __shared__ __align__(16) float2 s_buf[BUF];
+  __shared__ double s_red[32];
+  const int t = threadIdx.x;
+  DevState* ds = fp.ds;
+  for (int i = t; i < N; i += NTZ) s_tw[i] = fp.tw[i];
+  const long long L0 = (long long)blockIdx.x * LINES;
+  float2 v[C::RMAX];
+
+  if constexpr (MODE == Z_GRAD || MODE == Z_C2R || MODE == Z_SUMS) {
+    const float2* src = (MODE == Z_C2R) ? za.src : fp.W;
+    const float4* s4 = reinterpret_cast<const float4*>(src + L0 * ZP);
+    float4* b4 = reinterpret_cast<float4*>(s_buf);
+    for (int i = t; i < LINES * ZP / 2; i += NTZ) b4[i] = s4[i];
+    __syncthreads();
+    {
+      const int f = t / R2, a = t % R2;
+      if (f < 16) {
+#pragma unroll
+        for (int b = 0; b < R1; ++b) {
+          const int k = a + R2 * b;
+          float2 xa, xb;
+          if (k <= H) {
+            xa = s_buf[(2 * f) * ZP + k];
+            xb = s_buf[(2 * f + 1) * ZP + k];
+            if (k == 0 || k == H) { xa.y = 0.f; xb.y = 0.f; }
+          } else {
+            xa = cconj(s_buf[(2 * f) * ZP + N - k]);
+            xb = cconj(s_buf[(2 * f + 1) * ZP + N - k]);
+          }
+          v[b] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        }
+      }
+    }
+    __syncthreads();
+    fft2<N, R2, R1, INV, MAP_ROW, 16>(v, s_buf, s_tw, t);
+  } else {
+    float* sr = reinterpret_cast<float*>(s_buf);
+    if constexpr (MODE == Z_NOISE) {
+      const unsigned long long it = ds->iteration;
+      const uint64_t key = za.seed;
+      const unsigned long long blk0 = (unsigned long long)(L0 * N) / 8;
+      for (int q = t; q < LINES * N / 8; q += NTZ) {
+        P4 r = philox(blk0 + q, it, ST_MOMENTUM, 0, key);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float u1, u2;
+          u24pair(r.w[j], u1, u2);
+          const float rad = sqrtf(-2.f * logf(u1));
+          float sn, cs;
+          sincospif(2.f * u2, &sn, &cs);
+          sr[8 * q + 2 * j] = rad * cs;
+          sr[8 * q + 2 * j + 1] = rad * sn;
+        }
+      }
+    } else {
+      const float4* r4 = reinterpret_cast<const float4*>(za.rin + L0 * N);
+      float4* b4 = reinterpret_cast<float4*>(s_buf);
+      for (int i = t; i < LINES * N / 4; i += NTZ) b4[i] = r4[i];
+    }
+    __syncthreads();
+    const int f = t / R1, c = t % R1;
+    if (f < 16) {
+#pragma unroll
+      for (int d = 0; d < R2; ++d) {
+        const int n = c + R1 * d;
+        v[d] = make_float2(sr[(2 * f) * N + n], sr[(2 * f + 1) * N + n]);
+      }
+    }
+    __syncthreads();
+  }
+
+  // here: thread (f = t / R1, c = t % R1), f < 16, holds y[c + R1 d], d < R2
+  if constexpr (MODE == Z_GRAD || MODE == Z_C2R || MODE == Z_SUMS) {
+    const int f = t / R1, c = t % R1;
+    const long long la = (L0 + 2 * f) * N, lb = la + N;
+    if constexpr (MODE == Z_C2R) {
+      if (f < 16) {
+#pragma unroll
+        for (int d = 0; d < R2; ++d) {
+          const int n = c + R1 * d;
+          za.rout[la + n] = v[d].x * fp.inv_nv;
+          za.rout[lb + n] = v[d].y * fp.inv_nv;
+        }
+      }
+      return;
+    }
+    if constexpr (MODE == Z_SUMS) {
+      const long long nv = (long long)N * N * N;
+      for (int l = 0; l < fp.n_sub; ++l) {
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if (f < 16) {
+          const uint16_t* cn = fp.cnt + l * nv;
+          const float* rr = fp.R + l * nv;
+#pragma unroll
+          for (int d = 0; d < R2; ++d) {
+            const int n = c + R1 * d;
+            const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
+            const float ra = rr[la + n], rb = rr[lb + n];
+            s1 += (float)cn[la + n] * da + (float)cn[lb + n] * db;
+            s2 += ra * da + rb * db;
+            s3 += ra * da * da + rb * db * db;
+          }
+        }
+        double t1 = block_sum<NTZ>((double)s1, s_red);
+        double t2 = block_sum<NTZ>((double)s2, s_red);
+        double t3 = block_sum<NTZ>((double)s3, s_red);
+        if (t == 0) {
+          fp.part[za.region + (3 * l + 0) * fp.part_stride + blockIdx.x] = t1;
+          fp.part[za.region + (3 * l + 1) * fp.part_stride + blockIdx.x] = t2;
+          fp.part[za.region + (3 * l + 2) * fp.part_stride + blockIdx.x] = t3;
+        }
+      }
+      return;
+    }
+    // Z_GRAD: the local force g = a delta - c (Eq. Wiener_Posterior_force) and the
+    // likelihood energy (1/2) sum (a delta^2 - 2 c delta)
+    float e = 0.f;
+    if (f < 16) {
+      float aa[C::RMAX], ca[C::RMAX], ab[C::RMAX], cb[C::RMAX];
+#pragma unroll
+      for (int d = 0; d < R2; ++d) {
+        const int n = c + R1 * d;
+        aa[d] = fp.a[la + n];
+        ca[d] = fp.c[la + n];
+        ab[d] = fp.a[lb + n];
+        cb[d] = fp.c[lb + n];
+      }
+#pragma unroll
+      for (int d = 0; d < R2; ++d) {
+        const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
+        const float ga = fmaf(aa[d], da, -ca[d]), gb = fmaf(ab[d], db, -cb[d]);
+        e += da * (ga - ca[d]) + db * (gb - cb[d]);   // a d^2 - 2 c d
+        v[d] = make_float2(ga, gb);
+      }
+    }
+    if (za.region >= 0) {
+      double s = block_sum<NTZ>(0.5 * (double)e, s_red);
+      if (t == 0) fp.part[za.region + blockIdx.x] = s;
+    }
+  }
+
+  // forward transform of the packed pair, then split into the two half spectra
+  fft2<N, R1, R2, FWD, MAP_ROW, 16>(v, s_buf, s_tw, t);
+  {
+    const int f = t / R2, c = t % R2;
+    if (f < 16) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) s_buf[f * N + c + R2 * d] = v[d];
+    }
+  }
+  __syncthreads();
+  float2* dst = (MODE == Z_GRAD) ? fp.W : za.dst;
+  for (int i = t; i < LINES * (H + 1); i += NTZ) {
+    const int l = i / (H + 1), k = i - l * (H + 1);
+    const int f = l >> 1;
+    const float2 yk = s_buf[f * N + k];
+    const float2 ym = cconj(s_buf[f * N + (k == 0 ? 0 : N - k)]);
+    float2 g;
+    if ((l & 1) == 0) g = make_float2(0.5f * (yk.x + ym.x), 0.5f * (yk.y + ym.y));
+    else g = make_float2(0.5f * (yk.y - ym.y), -0.5f * (yk.x - ym.x));
+    dst[(L0 + l) * ZP + k] = g;
+  }
+}
+
+// ------------------------------------------------------------------ voxel kernels
+// a_i = sum_l b_l^2 Nbar_l R^l_i,  c_i = sum_l b_l (N^l_i - Nbar_l R^l_i)  (Eq. Wiener_Posterior_force);
+// the counts are zero wherever R = 0 (checked by set_data), so no mask is needed.
+__global__ void __launch_bounds__(256) k_rebuild(Fields fp, long long nv, int region) {
+  __shared__ float s_a[MAXS], s_b[MAXS], s_bn[MAXS];
+  __shared__ double s_red[32];
+  DevState* ds = fp.ds;
+  if (threadIdx.x < fp.n_sub) {
+    const double b = ds->b[threadIdx.x], nb = ds->nbar[threadIdx.x];
+    s_a[threadIdx.x] = (float)(b * b * nb);
+    s_b[threadIdx.x] = (float)b;
+    s_bn[threadIdx.x] = (float)(b * nb);
+  }
+  __syncthreads();
+  double acc = 0.0;
+  const long long n4 = nv / 4;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
+    float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Cc = A;
+    for (int l = 0; l < fp.n_sub; ++l) {
+      const float4 r = reinterpret_cast<const float4*>(fp.R + l * nv)[i];
+      const ushort4 n = reinterpret_cast<const ushort4*>(fp.cnt + l * nv)[i];
+      const float ka = s_a[l], kb = s_b[l], kbn = s_bn[l];
+      A.x = fmaf(ka, r.x, A.x); A.y = fmaf(ka, r.y, A.y); A.z = fmaf(ka, r.z, A.z); A.w = fmaf(ka, r.w, A.w);
+      Cc.x += kb * (float)n.x - kbn * r.x;
+      Cc.y += kb * (float)n.y - kbn * r.y;
+      Cc.z += kb * (float)n.z - kbn * r.z;
+      Cc.w += kb * (float)n.w - kbn * r.w;
+    }
+    reinterpret_cast<float4*>(fp.a)[i] = A;
+    reinterpret_cast<float4*>(fp.c)[i] = Cc;
+    acc += (double)A.x + (double)A.y + (double)A.z + (double)A.w;
+  }
+  double s = block_sum<256>(acc, s_red);
+  if (threadIdx.x == 0) fp.part[region + blockIdx.x] = s;
+}
+
+// Data check and compression: counts int32 -> uint16, R copied; per block the
+// sums R, N^2/R, #(R>0) over R > 0 and the number of invalid voxels.
+__global__ void __launch_bounds__(256) k_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout,
+                                              long long nv, double* part, int stride) {
+  __shared__ double s_red[32];
+  double sR = 0.0, sB = 0.0, no = 0.0, bad = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nv; i += (long long)gridDim.x * 256) {
+    const float r = rin[i];
+    const int n = cin[i];
+    const bool rok = (r >= 0.f) && isfinite(r);
+    const bool nok = n >= 0 && n <= 65535;
+    if (!rok || !nok || (r == 0.f && n > 0)) bad += 1.0;
+    cout[i] = (uint16_t)(nok ? n : 0);
+    rout[i] = rok ? r : 0.f;
+    if (rok && r > 0.f) {
+      sR += r;
+      sB += (double)n * (double)n / (double)r;
+      no += 1.0;
+    }
+  }
+  double v0 = block_sum<256>(sR, s_red);
+  double v1 = block_sum<256>(sB, s_red);
+  double v2 = block_sum<256>(no, s_red);
+  double v3 = block_sum<256>(bad, s_red);
+  if (threadIdx.x == 0) {
+    part[0 * stride + blockIdx.x] = v0;
+    part[1 * stride + blockIdx.x] = v1;
+    part[2 * stride + blockIdx.x] = v2;
+    part[3 * stride + blockIdx.x] = v3;
+  }
+}
+
+__global__ void k_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
+                               uint64_t* out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i * 4 >= n) return;
+  P4 r = philox(blk0 + i, it, stage, sub, seed);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (i * 4 + j < n) out[i * 4 + j] = r.w[j];
+}
+
+__global__ void k_voxel_normals(uint64_t seed, uint64_t it, size_t n, float* out) {
+  const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (q * 8 >= n) return;
+  P4 r = philox(q, it, ST_MOMENTUM, 0, seed);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float u1, u2;
+    u24pair(r.w[j], u1, u2);
+    const float rad = sqrtf(-2.f * logf(u1));
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    if (q * 8 + 2 * j < n) out[q * 8 + 2 * j] = rad * cs;
+    if (q * 8 + 2 * j + 1 < n) out[q * 8 + 2 * j + 1] = rad * sn;
+  }
+}
+
+// ------------------------------------------------------------------ launch tables
+template <int N>
+struct Launch {
+  using C = Cfg<N>;
+  template <int M>
+  static void x(const Fields& fp, const XArgs& xa, cudaStream_t s) {
+    k_xpass<N, M><<<C::TILES, C::NT, 0, s>>>(fp, xa);
+  }
+  template <int D>
+  static void y(const Fields& fp, float2* buf, cudaStream_t s) {
+    k_ypass<N, D><<<C::TILES, C::NT, 0, s>>>(fp, buf);
+  }
+  template <int M>
+  static void z(const Fields& fp, const ZArgs& za, cudaStream_t s) {
+    k_zpass<N, M><<<C::ZTILES, C::NTZ, 0, s>>>(fp, za);
+  }
+};
+
+template <int N>
+static PassTable make_table() {
+  using L = Launch<N>;
+  using C = Cfg<N>;
+  PassTable T;
+  T.N = N;
+  T.zp = C::ZP;
+  T.x_tiles = C::TILES;
+  T.z_tiles = C::ZTILES;
+  T.x_init = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_INIT>(f, XArgs{nullptr, nullptr, 0, region}, s); };
+  T.x_leap = [](const Fields& f, int first, cudaStream_t s) { L::template x<X_LEAP>(f, XArgs{nullptr, nullptr, first, -1}, s); };
+  T.x_final = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_FINAL>(f, XArgs{nullptr, nullptr, 0, region}, s); };
+  T.x_inv = [](const Fields& f, const float2* src, float2* dst, cudaStream_t s) { L::template x<X_INV>(f, XArgs{src, dst, 0, -1}, s); };
+  T.x_fwd = [](const Fields& f, const float2* src, float2* dst, cudaStream_t s) { L::template x<X_FWD>(f, XArgs{src, dst, 0, -1}, s); };
+  T.x_grad = [](const Fields& f, float2* dst, int region, cudaStream_t s) { L::template x<X_GRAD>(f, XArgs{nullptr, dst, 0, region}, s); };
+  T.x_jinv = [](const Fields& f, cudaStream_t s) { L::template x<X_JINV>(f, XArgs{nullptr, nullptr, 0, -1}, s); };
+  T.x_jgrad = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_JGRAD>(f, XArgs{nullptr, nullptr, 0, region}, s); };
+  T.x_scale = [](const Fields& f, cudaStream_t s) { L::template x<X_SCALE>(f, XArgs{nullptr, nullptr, 0, -1}, s); };
+  T.x_binpow = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_BINPOW>(f, XArgs{nullptr, nullptr, 0, region}, s); };
+  T.y_fwd = [](const Fields& f, float2* buf, cudaStream_t s) { L::template y<FWD>(f, buf, s); };
+  T.y_inv = [](const Fields& f, float2* buf, cudaStream_t s) { L::template y<INV>(f, buf, s); };
+  T.z_grad = [](const Fields& f, int region, cudaStream_t s) { L::template z<Z_GRAD>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, s); };
+  T.z_noise = [](const Fields& f, uint64_t seed, cudaStream_t s) { L::template z<Z_NOISE>(f, ZArgs{nullptr, f.ph, nullptr, nullptr, -1, seed}, s); };
+  T.z_r2c = [](const Fields& f, const float* rin, float2* dst, cudaStream_t s) { L::template z<Z_R2C>(f, ZArgs{nullptr, dst, rin, nullptr, -1, 0}, s); };
+  T.z_c2r = [](const Fields& f, const float2* src, float* rout, cudaStream_t s) { L::template z<Z_C2R>(f, ZArgs{src, nullptr, nullptr, rout, -1, 0}, s); };
+  T.z_sums = [](const Fields& f, int region, cudaStream_t s) { L::template z<Z_SUMS>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, s); };
+  return T;
+}
+
+bool pass_table(int N, PassTable* out) {
+  switch (N) {
+    case 8: *out = make_table<8>(); return true;
+    case 16: *out = make_table<16>(); return true;
+    case 32: *out = make_table<32>(); return true;
+    case 64: *out = make_table<64>(); return true;
+    case 96: *out = make_table<96>(); return true;
+    case 128: *out = make_table<128>(); return true;
+    case 256: *out = make_table<256>(); return true;
+    default: return false;
+  }
+}
+
+void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, cudaStream_t s) {
+  k_rebuild<<<blocks, 256, 0, s>>>(fp, nv, region);
+}
+void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
+                 int stride, int blocks, cudaStream_t s) {
+  k_data<<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride);
+}
+void launch_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
+                         uint64_t* out, cudaStream_t s) {
+  size_t nb = (n + 3) / 4;
+  k_philox_words<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(seed, it, stage, sub, blk0, n, out);
+}
+void launch_voxel_normals(uint64_t seed, uint64_t it, size_t n, float* out, cudaStream_t s) {
+  size_t nb = (n + 7) / 8;
+  k_voxel_normals<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(seed, it, n, out);
+}
+
+}  // namespace bps

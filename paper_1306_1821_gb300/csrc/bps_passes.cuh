@@ -1,0 +1,183 @@
+// Field passes of the sampler: each pass moves one axis of the 3D transform
+// through shared memory and fuses the pointwise work of the method into it.
+//
+// Layout in HBM: real fields [N][N][N] float32, x slowest; half spectra
+// [N][N][ZP] complex64 with ZP = N/2+1 rounded up to an even count (16-byte
+// aligned rows; the pad column is never read as data).  A 3D transform is three
+// passes:  z (contiguous lines, real <-> half spectrum, two real lines packed in
+// one complex line), y (stride ZP) and x (stride N*ZP).  The strided passes
+// work on tiles of F adjacent columns by all N rows; the Nyquist column
+// kz = N/2 has its own tiles whose F columns are adjacent rows of the other
+// transverse axis.
+//
+// One transform of length N = R1*R2 is split across threads: a register DFT of
+// one factor, a twiddle by W_N^(j c), one exchange through shared memory, a
+// register DFT of the other factor.  Global loads and stores of every pass go
+// straight between registers and HBM in the order a warp reads contiguously.
+#pragma once
+#include "bps_common.cuh"
+
+namespace bps {
+
+// ------------------------------------------------------------ pass arguments
+struct Fields {
+  float2* dh[2];          // state double buffer (DevState::cur selects the current one)
+  float2* ph;             // momentum half spectrum
+  float2* W;              // work half spectrum
+  float* a;               // local curvature  a = sum_l b_l^2 Nbar_l R^l
+  float* c;               // local drive      c = sum_l b_l (N^l - Nbar_l R^l)
+  const uint16_t* cnt;    // counts [n_sub][N^3]
+  const float* R;         // response [n_sub][N^3]
+  int n_sub;
+  DevState* ds;
+  double* part;           // per-block partial sums (FP64)
+  int part_stride;        // doubles between consecutive quantities of one region
+  const float2* tw;       // W_N^j = exp(-2 pi i j / N), j < N (FP64-rounded)
+  float inv_nv;           // 1 / N^3
+  int mass_mode;
+};
+
+enum { MAP_COL = 0, MAP_ROW = 1 };
+
+template <int MAP, int A, int B, int F>
+__device__ __forceinline__ int exidx(int f, int a, int c) {
+  if constexpr (MAP == MAP_COL) return (c * A + a) * F + f;
+  else return f * (B * (A + 1)) + c * (A + 1) + a;
+}
+
+// Transform of length N = A*B over F independent columns.
+// In : thread (f, j<A) holds v[b] = x[j + A b], b < B.
+// Out: thread (f, j<B) holds v[d] = X[j + B d], d < A.
+// MAP_COL: f = t % F, j = t / F.   MAP_ROW: f = t / (A or B), j = t % (A or B).
+template <int N, int A, int B, int DIR, int MAP, int F>
+__device__ __forceinline__ void fft2(float2* v, float2* ex, const float2* tw, int t) {
+  int f, j;
+  if constexpr (MAP == MAP_COL) { f = t % F; j = t / F; } else { f = t / A; j = t % A; }
+  if (j < A && f < F) {
+    Dft<B, DIR>::run(v);
+#pragma unroll
+    for (int c = 1; c < B; ++c) {
+      float2 w = tw[j * c];
+      if constexpr (DIR == INV) w.y = -w.y;
+      v[c] = cmul(v[c], w);
+    }
+#pragma unroll
+    for (int c = 0; c < B; ++c) ex[exidx<MAP, A, B, F>(f, j, c)] = v[c];
+  }
+  __syncthreads();
+  if constexpr (MAP == MAP_COL) { f = t % F; j = t / F; } else { f = t / B; j = t % B; }
+  if (j < B && f < F) {
+#pragma unroll
+    for (int a = 0; a < A; ++a) v[a] = ex[exidx<MAP, A, B, F>(f, a, j)];
+    Dft<A, DIR>::run(v);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ tile geometry
+// Strided pass over axis X (rows = kx) or Y (rows = ky).
+template <int N>
+struct Tile {
+  long long base, rs, cs;   // element (row r, column f) at base + r*rs + f*cs
+  int ky0, kz0, kx0;        // transverse coordinates of column 0
+  int dky, dkz, dkx;        // increments per column
+};
+
+template <int N>
+__device__ __forceinline__ Tile<N> tile_x(int id) {
+  using C = Cfg<N>;
+  Tile<N> T;
+  T.rs = (long long)N * C::ZP;
+  T.kx0 = 0; T.dkx = 0;
+  if (id < N * C::ZB) {
+    int y = id / C::ZB, zb = id % C::ZB;
+    T.base = (long long)y * C::ZP + zb * C::F; T.cs = 1;
+    T.ky0 = y; T.dky = 0; T.kz0 = zb * C::F; T.dkz = 1;
+  } else {
+    int yb = id - N * C::ZB;
+    T.base = (long long)yb * C::F * C::ZP + C::H; T.cs = C::ZP;
+    T.ky0 = yb * C::F; T.dky = 1; T.kz0 = C::H; T.dkz = 0;
+  }
+  return T;
+}
+
+template <int N>
+__device__ __forceinline__ Tile<N> tile_y(int id) {
+  using C = Cfg<N>;
+  Tile<N> T;
+  T.rs = C::ZP;
+  T.ky0 = 0; T.dky = 0;
+  if (id < N * C::ZB) {
+    int x = id / C::ZB, zb = id % C::ZB;
+    T.base = (long long)x * N * C::ZP + zb * C::F; T.cs = 1;
+    T.kx0 = x; T.dkx = 0; T.kz0 = zb * C::F; T.dkz = 1;
+  } else {
+    int xb = id - N * C::ZB;
+    T.base = (long long)xb * C::F * N * C::ZP + C::H; T.cs = (long long)N * C::ZP;
+    T.kx0 = xb * C::F; T.dkx = 1; T.kz0 = C::H; T.dkz = 0;
+  }
+  return T;
+}
+
+template <int N>
+__device__ __forceinline__ int sgn_n(int k) { return k <= N / 2 ? k : k - N; }
+
+// Bin of |n|^2 from the table of each bin's smallest |n|^2 (padded with INT_MAX
+// to 64 entries); -1 for the DC mode.
+__device__ __forceinline__ int bin_of(int n2, const int* thr) {
+  if (n2 == 0) return -1;
+  int lo = 0;
+#pragma unroll
+  for (int s = 32; s > 0; s >>= 1)
+    if (thr[lo + s] <= n2) lo += s;
+  return lo;
+}
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum; result valid in thread 0.  sh: >= 32 doubles.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < (NT + 31) / 32; ++i) r += sh[i];
+  }
+  return r;
+}
+
+// Per-bin accumulation for one element per thread of a column tile: within
+// each group of G consecutive lanes (one tile row) the bin is monotone along
+// the lanes, so lanes of one bin are contiguous; a segmented shuffle sum gives
+// the segment total to its first lane, which adds it to the warp's own bins.
+// Groups of one warp add in a fixed order: the result is deterministic.
+template <int G>
+__device__ __forceinline__ void bin_accumulate(float v, int m, double* wbins) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % G;
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    float pv = __shfl_down_sync(0xffffffffu, v, o);
+    int pm = __shfl_down_sync(0xffffffffu, m, o);
+    if (gl + o < G && pm == m) v += pv;
+  }
+  int prev = __shfl_up_sync(0xffffffffu, m, 1);
+  bool head = (gl == 0) || (prev != m);
+#pragma unroll
+  for (int g = 0; g < 32 / G; ++g) {
+    if (lane / G == g && head && m >= 0) wbins[m] += (double)v;
+    __syncwarp();
+  }
+}
+
+}  // namespace bps
