@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of the sampler's hot path on GB300.
+
+One step = one full Gibbs iteration of the multiple-block scan at 256^3
+(L = 1000 Mpc/h, six luminosity subsamples, 32 k bins): an HMC move of the
+density field with 20 leapfrog steps, the power-spectrum draw, the P-delta jump
+(10 leapfrog steps in ln P), the bias and normalisation draws and the rebuild of
+the local fields.  The metric counts the density-field leapfrog steps (20 per
+step); everything else in the iteration is inside the timed region too.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own chain on its own GPU (replicas:
+the single-chain path has no data-parallel split), the time is the maximum over
+ranks and the value the total over ranks.  Rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HMC leapfrog steps/sec and P(k) effective samples/sec at 256³ vs plain FP32"
+UNIT = "leapfrog steps/s"
+WORKLOAD = "survey256"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "xleap_survey256_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1306_1821_gb300", "csrc", f)
+                  for f in ("bps_passes.cu", "bps_passes.cuh", "bps_common.cuh")]
+KERNEL_NAMES = ["x pass (kick+drift+IFFT_x)", "y pass inverse", "z pass (C2R, local force, R2C)", "y pass forward"]
+
+
+# ---------------------------------------------------------------- helpers
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(seconds, units, world_size, device=None):
+    """(max seconds over ranks, sum of units over ranks); identity for one rank."""
+    if world_size <= 1:
+        return float(seconds), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unavailable"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_traffic():
+    """DRAM bytes per x-pass launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    kv = {}
+    with open(PROFILE_TRAFFIC) as f:
+        for ln in f:
+            if "=" in ln and not ln.startswith("#"):
+                k, v = ln.split("=", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("kernel_hash") != kernel_hash():
+        return None
+    try:
+        return float(kv["bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- oracle (CPU) leg
+def oracle_leapfrog_rate(wl, counts, R, n_steps=2):
+    """The FP64 oracle's leapfrog on host cores: n_steps leapfrog steps of one
+    trajectory (n_steps + 1 force evaluations) at the full workload."""
+    import numpy as np
+
+    from oracle import grid, hmc, model
+    from paper_1306_1821_gb300 import inputs
+    geom = grid.Geometry(wl.N, wl.box, wl.n_bins)
+    P, b, nbar = inputs.initial_state(wl)
+    a, c = model.local_fields(counts, R, b, nbar)
+    M, invM = model.mass_diag(geom, P, float(a.mean()))
+    dh = np.zeros((wl.N, wl.N, wl.N // 2 + 1), dtype=np.complex128)
+    p0 = hmc.draw_momentum(geom, M, 1, 0)
+    t0 = time.perf_counter()
+    hmc.leapfrog(geom, dh, p0, 0.1, n_steps, P, a, c, invM)
+    dt = time.perf_counter() - t0
+    return n_steps / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1306_1821_gb300 import inputs
+    wl = inputs.WORKLOADS[WORKLOAD]
+    _, counts, R = inputs.make_survey(wl)
+    steps = min(args.steps, 20)
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        oracle_leapfrog_rate(wl, counts, R, n_steps=1)
+    tot = 0.0
+    for _ in range(steps):
+        _, dt = oracle_leapfrog_rate(wl, counts, R, n_steps=1)
+        tot += dt
+    value = steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(wl, "cpu"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} single leapfrog steps of one trajectory at 256^3 (2 force "
+                                   f"evaluations each, numpy FP64 FFT, one thread), after {warm} warm-up"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(wl, where):
+    return {"workload": f"{wl.name}: {wl.N}^3 grid, L={wl.box:g} Mpc/h, {wl.n_sub} subsamples, "
+                        f"{wl.n_bins} k bins, {wl.n_leapfrog} leapfrog steps per HMC move, jump on "
+                        f"({wl.jump_leapfrog} steps), one Gibbs iteration per step",
+            "grid": wl.N, "box_mpc_h": wl.box, "n_sub": wl.n_sub, "n_bins": wl.n_bins,
+            "leapfrog_per_step": wl.n_leapfrog, "jump_leapfrog_per_step": wl.jump_leapfrog,
+            "l2": "inputs larger than L2 (each half spectrum 68 MB, 0.95 GB moved per leapfrog)",
+            "parallelism": "replicas (one chain per GPU)" if where != "cpu" else "single host thread"}
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1306_1821_gb300 import bps, inputs
+    if not os.path.exists(bps.LIB_PATH):
+        from paper_1306_1821_gb300 import build as b
+        b.build()
+    bps.load()
+
+    wl = inputs.WORKLOADS[WORKLOAD]
+    delta, counts, R = inputs.make_survey(wl, seed=wl.seed + rank)
+    P0, b0, nbar0 = inputs.initial_state(wl)
+    stream = torch.cuda.Stream(device=dev)
+    s = bps.Sampler(wl.N, wl.box, wl.n_sub, wl.n_bins, stream=stream, n_leapfrog=wl.n_leapfrog,
+                    eps_max=wl.eps_max, jump=1, jump_leapfrog=wl.jump_leapfrog, jump_eps_max=wl.jump_eps_max,
+                    fixed_bias_index=wl.fixed_bias, seed=1 + rank)
+    with torch.cuda.stream(stream):
+        cnt_d = torch.from_numpy(counts).to(dev)
+        R_d = torch.from_numpy(R).to(dev)
+        d_d = torch.from_numpy(delta.astype(np.float32)).to(dev)
+    stream.synchronize()
+    bps.bps_set_data(s.ctx, cnt_d, R_d)
+    bps.bps_set_state(s.ctx, d_d, P0, b0, nbar0, 0)
+    del cnt_d, R_d, d_d
+
+    # warm-up iterations (also moves the chain off its starting point)
+    if args.warmup > 0:
+        bps.bps_gibbs_iterate(s.ctx, args.warmup)
+
+    # ---- device-timed region: K Gibbs iterations, inputs resident in HBM
+    bps.bps_profile(s.ctx, 1)
+    bps.bps_profile_read(s.ctx)
+    l0 = bps.bps_kernel_launches(s.ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        rec = bps.bps_gibbs_iterate(s.ctx, args.steps, s.rec_len)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = bps.bps_kernel_launches(s.ctx) - l0
+    kms, kn = bps.bps_profile_read(s.ctx)
+    bps.bps_profile(s.ctx, 0)
+    local_s = e0.elapsed_time(e1) / 1000.0
+    secs, units = aggregate(local_s, args.steps * wl.n_leapfrog, ws, dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    acc_rate = float(np.mean(rec[:, -1])) if len(rec) else float("nan")
+
+    # ---- end to end through the public API with host buffers: upload the
+    # survey from pinned memory, one Gibbs iteration, read the chain record back
+    k_e2e = min(args.steps, 20)
+    cnt_h = torch.from_numpy(counts).pin_memory().numpy()
+    R_h = torch.from_numpy(R).pin_memory().numpy()
+    rec_h = torch.zeros(s.rec_len, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        bps.bps_set_data_host(s.ctx, cnt_h, R_h)
+        out = bps.bps_gibbs_iterate(s.ctx, 1, s.rec_len)
+        rec_h[:] = out[0]
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e_secs, e2e_units = aggregate(e2e_s, k_e2e * wl.n_leapfrog, ws, dev)
+
+    # ---- roofline of the dominant kernel (the x pass), from the live events
+    S_c = wl.N * wl.N * (wl.N // 2 + 1) * 8
+    S_r = wl.N ** 3 * 4
+    bytes_kind = [6 * S_c, 2 * S_c, 2 * S_c + 2 * S_r, 2 * S_c]
+    per_launch_ms = [kms[i] / max(kn[i], 1) for i in range(4)]
+    shares = [kms[i] / max(sum(kms), 1e-30) for i in range(4)]
+    peak, peak_kind = measured_peaks()
+    dom = int(np.argmax(kms))
+    achieved = bytes_kind[dom] / (per_launch_ms[dom] * 1e-3) / 1e9
+    leap_ms = sum(per_launch_ms)
+    leap_bytes = 12 * S_c + 2 * S_r
+    traffic = read_traffic() if dom == 0 else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": units / secs,
+            "unit": UNIT,
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1000.0 * secs / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": config_dict(wl, "gpu"),
+            "gibbs_iterations_per_s": ws * args.steps / secs,
+            "hmc_acceptance": acc_rate,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": KERNEL_NAMES[dom], "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+                         if peak_kind == "measured" else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": bytes_kind[dom], "launch_ms": per_launch_ms[dom]},
+            "leapfrog_kernels": {KERNEL_NAMES[i]: {"ms": per_launch_ms[i], "launches": int(kn[i]),
+                                                   "share": shares[i],
+                                                   "GBps": bytes_kind[i] / (per_launch_ms[i] * 1e-3) / 1e9}
+                                 for i in range(4)},
+            "leapfrog_roofline": {"bytes": leap_bytes, "ms": leap_ms,
+                                  "GBps": leap_bytes / (leap_ms * 1e-3) / 1e9,
+                                  "frac": leap_bytes / (leap_ms * 1e-3) / 1e9 / peak},
+            "e2e": {"value": e2e_units / e2e_secs, "unit": UNIT,
+                    "h2d_bytes_per_step": int(counts.nbytes + R.nbytes),
+                    "d2h_bytes_per_step": int(8 * s.rec_len)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            v, dt = oracle_leapfrog_rate(wl, counts, R, n_steps=2)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"2 leapfrog steps (3 force evaluations) of one trajectory at "
+                                              f"256^3 with 6 subsamples, FP64 numpy on one host thread, "
+                                              f"{dt:.1f} s"}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -191,6 +191,16 @@ const char* bps_last_error(const bps_ctx* ctx);
 /* Number of kernels this context has launched (for launch accounting). */
 uint64_t bps_kernel_launches(const bps_ctx* ctx);
 
+/* Per-kernel timing of the leapfrog passes of bps_hmc_step / bps_gibbs_iterate:
+ * with enable = 1 the library records a CUDA event pair around every launch of
+ * the four leapfrog kernels (0: x pass with kick/drift, 1: y inverse, 2: z pass
+ * with the local force, 3: y forward) on the context's stream.
+ * bps_profile_read synchronises the stream and returns, per kernel kind, the
+ * summed device milliseconds ms[4] and the launch counts n[4] since the last
+ * read (then resets them).  Timing only; results are unchanged. */
+bps_status bps_profile(bps_ctx* ctx, int enable);
+bps_status bps_profile_read(bps_ctx* ctx, double* ms, uint64_t* n);
+
 void bps_destroy(bps_ctx* ctx);
 
 #ifdef __cplusplus

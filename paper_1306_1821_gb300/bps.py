@@ -62,6 +62,8 @@ _SIGS = {
     "bps_version": ([], ctypes.c_char_p),
     "bps_last_error": ([_P], ctypes.c_char_p),
     "bps_kernel_launches": ([_P], ctypes.c_uint64),
+    "bps_profile": ([_P, ctypes.c_int], ctypes.c_int),
+    "bps_profile_read": ([_P, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "bps_destroy": ([_P], None),
 }
 
@@ -250,6 +252,17 @@ def bps_version():
 
 def bps_kernel_launches(ctx):
     return int(load().bps_kernel_launches(ctx))
+
+
+def bps_profile(ctx, enable):
+    _check(ctx, load().bps_profile(ctx, int(enable)))
+
+
+def bps_profile_read(ctx):
+    ms = np.zeros(4)
+    n = (ctypes.c_uint64 * 4)()
+    _check(ctx, load().bps_profile_read(ctx, ms.ctypes.data_as(_D), n))
+    return ms, np.array(list(n), dtype=np.int64)
 
 
 class Sampler:

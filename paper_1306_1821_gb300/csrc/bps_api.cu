@@ -40,6 +40,12 @@ struct bps_ctx {
   bool have_data = false;
   int rebuild_blocks = 0;
   uint64_t launches = 0;
+  // leapfrog kernel timing (bps_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev[4];
+  size_t ev_used[4] = {0, 0, 0, 0};
+  double prof_ms[4] = {0, 0, 0, 0};
+  uint64_t prof_n[4] = {0, 0, 0, 0};
   std::string err;
 };
 
@@ -214,6 +220,34 @@ bps_status rebuild(bps_ctx* ctx) {
   return BPS_OK;
 }
 
+constexpr size_t PROF_CAP = 8192;   // event pairs per kernel kind before folding
+
+void prof_fold(bps_ctx* ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  for (int k = 0; k < 4; ++k) {
+    for (size_t i = 0; i + 1 < ctx->ev_used[k]; i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->ev[k][i], ctx->ev[k][i + 1]) == cudaSuccess) {
+        ctx->prof_ms[k] += ms;
+        ctx->prof_n[k] += 1;
+      }
+    }
+    ctx->ev_used[k] = 0;
+  }
+}
+
+// record one event of kernel kind k (start or end); no-op unless profiling
+void prof_mark(bps_ctx* ctx, int k) {
+  if (!ctx->prof) return;
+  if (ctx->ev_used[k] >= PROF_CAP && ctx->ev_used[k] % 2 == 0) prof_fold(ctx);
+  if (ctx->ev_used[k] == ctx->ev[k].size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    ctx->ev[k].push_back(e);
+  }
+  cudaEventRecord(ctx->ev[k][ctx->ev_used[k]++], ctx->stream);
+}
+
 // force of the current state into W (Fourier), likelihood energy partials in `lik_region`
 bps_status hmc_move(bps_ctx* ctx, bool advance) {
   Fields f = fields(ctx);
@@ -229,10 +263,18 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   P.z_grad(f, region_offset(ctx, RG_LIK0), s);
   P.y_fwd(f, ctx->W, s);
   for (int st = 1; st <= L; ++st) {
+    prof_mark(ctx, 0);
     P.x_leap(f, st == 1 ? 1 : 0, s);
+    prof_mark(ctx, 0);
+    prof_mark(ctx, 1);
     P.y_inv(f, ctx->W, s);
+    prof_mark(ctx, 1);
+    prof_mark(ctx, 2);
     P.z_grad(f, st == L ? region_offset(ctx, RG_LIK1) : -1, s);
+    prof_mark(ctx, 2);
+    prof_mark(ctx, 3);
     P.y_fwd(f, ctx->W, s);
+    prof_mark(ctx, 3);
   }
   P.x_final(f, region_offset(ctx, RG_FINAL), s);
   launch_move_end(sa, region_offset(ctx, RG_INIT), region_offset(ctx, RG_LIK0), region_offset(ctx, RG_FINAL),
@@ -350,6 +392,8 @@ int current_buffer(bps_ctx* ctx, bps_status* st) {
 }
 
 void free_all(bps_ctx* c) {
+  for (int k = 0; k < 4; ++k)
+    for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);
   cudaFree(c->dh[0]);
   cudaFree(c->dh[1]);
   cudaFree(c->ph);
@@ -375,6 +419,25 @@ const char* bps_version(void) { return "bps 0.1 (sm_103a)"; }
 const char* bps_last_error(const bps_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
 uint64_t bps_kernel_launches(const bps_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+bps_status bps_profile(bps_ctx* ctx, int enable) {
+  if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
+  if (ctx->prof && !enable) prof_fold(ctx);
+  ctx->prof = enable != 0;
+  return BPS_OK;
+}
+
+bps_status bps_profile_read(bps_ctx* ctx, double* ms, uint64_t* n) {
+  if (!ctx || !ms || !n) return fail(ctx, BPS_EINVAL, "null argument");
+  prof_fold(ctx);
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = ctx->prof_ms[k];
+    n[k] = ctx->prof_n[k];
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_n[k] = 0;
+  }
+  return BPS_OK;
+}
 
 bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* cfg, void* cuda_stream,
                       bps_ctx** out) {
@@ -409,6 +472,7 @@ bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* c
   ctx->Vc = std::pow(box_len / grid_n, 3);
   ctx->n_spec = (size_t)grid_n * grid_n * pt.zp;
   ctx->n_mass = cfg->n_bins;
+  ctx->chain_cap = 1024;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -422,6 +486,7 @@ bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* c
             alloc((void**)&ctx->tw, grid_n * sizeof(float2)) &&
             alloc((void**)&ctx->part, (size_t)region_total() * ctx->part_stride * sizeof(double)) &&
             alloc((void**)&ctx->ds, sizeof(DevState)) &&
+            alloc((void**)&ctx->chain_dev, (size_t)1024 * (cfg->n_bins + 2 * n_sub + 2) * sizeof(double)) &&
             cudaMallocHost((void**)&ctx->host_buf, 64 * 1024) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
