@@ -183,6 +183,30 @@ bps_status bps_philox_words(uint64_t seed, uint64_t iteration, uint64_t stage, u
 bps_status bps_voxel_normals(uint64_t seed, uint64_t iteration, size_t n, float* out_dev,
                              void* cuda_stream);
 
+/* k-bin power without device allocation.  The paper has no counterpart: this
+ * is a deployment variant of the sigma_m reduction behind bps_sample_power,
+ * for callers that may not allocate device memory at all, neither directly nor
+ * through this library (for example a host framework whose own pool must
+ * account for every device byte, or a loop that cannot afford cudaMalloc's
+ * implicit synchronisation).  It computes, for the half spectrum spec_dev
+ * (complex64 [N][N][N/2+1], device), sigma_m = (V_cell/N^3) sum_{k in m} w_k
+ * |spec_k|^2 into sigma_dev (n_bins doubles, device), with the bins of
+ * bps_create and w_k the half-spectrum multiplicity; nothing is drawn and no
+ * context is needed.  The caller passes input and output; the library keeps
+ * its per-block partial sums in one file-scope device array of 1024 x 64
+ * doubles (512 KiB), which every GPU that loads the library holds until the
+ * process exits.  Limits: N even in 4..512, 1 <= n_bins <= 64 (BPS_EINVAL
+ * beyond them, text in bps_last_error(NULL)).  The first call on each device,
+ * with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  No call allocates or frees anything.  All calls share the array:
+ * calls whose kernels overlap on the GPU (different streams, or other host
+ * threads) race and must be serialised by the caller.  Work is queued on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream); the call does not
+ * synchronise. */
+bps_status bps_bin_power_noalloc(int grid_n, double box_len, int n_bins, const float* spec_dev,
+                                 double* sigma_dev, void* cuda_stream);
+
 /* Library version string and the text of the last error of ctx (or of the
  * last failed context-free call when ctx is NULL). */
 const char* bps_version(void);

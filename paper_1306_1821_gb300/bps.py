@@ -64,6 +64,7 @@ _SIGS = {
     "bps_kernel_launches": ([_P], ctypes.c_uint64),
     "bps_profile": ([_P, ctypes.c_int], ctypes.c_int),
     "bps_profile_read": ([_P, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bps_bin_power_noalloc": ([ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "bps_destroy": ([_P], None),
 }
 
@@ -244,6 +245,12 @@ def bps_philox_words(seed, iteration, stage, sub, block0, out, stream=None):
 def bps_voxel_normals(seed, iteration, out, stream=None):
     _check(None, load().bps_voxel_normals(int(seed), int(iteration), int(out.numel()), _dptr(out),
                                           _stream_ptr(stream)))
+
+
+def bps_bin_power_noalloc(grid_n, box_len, n_bins, spec, sigma, stream=None):
+    """sigma (float64 CUDA tensor [n_bins]) <- k-bin power of spec, no device allocation."""
+    _check(None, load().bps_bin_power_noalloc(int(grid_n), float(box_len), int(n_bins), _dptr(spec), _dptr(sigma),
+                                              _stream_ptr(stream)))
 
 
 def bps_version():

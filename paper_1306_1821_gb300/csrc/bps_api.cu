@@ -411,6 +411,8 @@ void free_all(bps_ctx* c) {
 
 }  // namespace
 
+void bps::set_last_error(const char* msg) { g_err = msg; }
+
 // =================================================================== C ABI
 extern "C" {
 

@@ -66,4 +66,7 @@ void launch_zero_dc(float2* spec, cudaStream_t s);
 
 enum JumpKind { J_FIRST = 0, J_MID = 1, J_LAST = 2 };
 
+// Text returned by bps_last_error(NULL) for context-free calls.
+void set_last_error(const char* msg);
+
 }  // namespace bps
