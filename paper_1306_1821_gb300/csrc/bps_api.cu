@@ -39,6 +39,7 @@ struct bps_ctx {
   int n_mass = 0;
   bool have_data = false;
   int rebuild_blocks = 0;
+  int n_sm = 0;
   uint64_t launches = 0;
   // leapfrog kernel timing (bps_profile)
   bool prof = false;
@@ -116,6 +117,7 @@ Fields fields(bps_ctx* c) {
   f.tw = c->tw;
   f.inv_nv = (float)(1.0 / (double)c->nv);
   f.mass_mode = c->cfg.mass_mode;
+  f.n_sm = c->n_sm;
   return f;
 }
 
@@ -204,6 +206,7 @@ bps_status check_status(bps_ctx* ctx) {
   if (st != 0) {
     int zero = 0;
     ds_write_bytes(ctx, DS_OFF(status), &zero, sizeof(int));
+    if (st & ST_TIMEOUT) return fail(ctx, BPS_ETIMEOUT, "a tile copy did not complete within the wait limit");
     if (st & ST_NONFINITE) return fail(ctx, BPS_ENUMERIC, "non-finite energy difference; move rejected");
     return fail(ctx, BPS_ENUMERIC, "a scalar draw failed (no acceptance within the attempt bound or a non-positive sum)");
   }
@@ -257,23 +260,23 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   const int L = ctx->cfg.n_leapfrog;
   launch_move_begin(sa, s);
   P.z_noise(f, ctx->cfg.seed, s);
-  P.y_fwd(f, ctx->ph, s);
+  P.y_fwd(f, BUF_PH, s);
   P.x_init(f, region_offset(ctx, RG_INIT), s);
-  P.y_inv(f, ctx->W, s);
+  P.y_inv(f, BUF_W, s);
   P.z_grad(f, region_offset(ctx, RG_LIK0), s);
-  P.y_fwd(f, ctx->W, s);
+  P.y_fwd(f, BUF_W, s);
   for (int st = 1; st <= L; ++st) {
     prof_mark(ctx, 0);
     P.x_leap(f, st == 1 ? 1 : 0, s);
     prof_mark(ctx, 0);
     prof_mark(ctx, 1);
-    P.y_inv(f, ctx->W, s);
+    P.y_inv(f, BUF_W, s);
     prof_mark(ctx, 1);
     prof_mark(ctx, 2);
     P.z_grad(f, st == L ? region_offset(ctx, RG_LIK1) : -1, s);
     prof_mark(ctx, 2);
     prof_mark(ctx, 3);
-    P.y_fwd(f, ctx->W, s);
+    P.y_fwd(f, BUF_W, s);
     prof_mark(ctx, 3);
   }
   P.x_final(f, region_offset(ctx, RG_FINAL), s);
@@ -307,8 +310,8 @@ bps_status bias_stage(bps_ctx* ctx, bool advance) {
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
   // delta = C2R(delta_hat) (x and y inverse into W), the per-subsample sums in the z pass
-  ctx->pt.x_inv(f, nullptr, ctx->W, s);
-  ctx->pt.y_inv(f, ctx->W, s);
+  ctx->pt.x_inv(f, -1, ctx->W, s);
+  ctx->pt.y_inv(f, BUF_W, s);
   ctx->pt.z_sums(f, region_offset(ctx, RG_SUMS), s);
   launch_bias_nbar(sa, region_offset(ctx, RG_SUMS), ctx->pt.z_tiles, s);
   LAUNCHED(ctx, 4);
@@ -328,9 +331,9 @@ bps_status jump_gradient(bps_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   const PassTable& P = ctx->pt;
   P.x_jinv(f, s);
-  P.y_inv(f, ctx->W, s);
+  P.y_inv(f, BUF_W, s);
   P.z_grad(f, region_offset(ctx, RG_JLIK), s);
-  P.y_fwd(f, ctx->W, s);
+  P.y_fwd(f, BUF_W, s);
   P.x_jgrad(f, region_offset(ctx, RG_JGRAD), s);
   launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), P.z_tiles, s);
   LAUNCHED(ctx, 6);
@@ -479,6 +482,7 @@ bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* c
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   ctx->rebuild_blocks = sms > 0 ? 4 * sms : 512;
+  ctx->n_sm = sms > 0 ? sms : 148;
   ctx->part_stride = std::max(std::max(pt.x_tiles, pt.z_tiles), ctx->rebuild_blocks);
 
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
@@ -636,8 +640,8 @@ bps_status bps_set_state(bps_ctx* ctx, const float* delta_dev, const double* P, 
   Fields f = fields(ctx);
   if (delta_dev) {
     ctx->pt.z_r2c(f, delta_dev, ctx->W, ctx->stream);
-    ctx->pt.y_fwd(f, ctx->W, ctx->stream);
-    ctx->pt.x_fwd(f, ctx->W, nullptr, ctx->stream);
+    ctx->pt.y_fwd(f, BUF_W, ctx->stream);
+    ctx->pt.x_fwd(f, BUF_W, nullptr, ctx->stream);
     LAUNCHED(ctx, 3);
     int cur = current_buffer(ctx, &st);
     if (st != BPS_OK) return st;
@@ -657,8 +661,8 @@ bps_status bps_get_state(bps_ctx* ctx, float* delta_dev, double* P, double* b, d
   bps_status st = BPS_OK;
   if (delta_dev) {
     Fields f = fields(ctx);
-    ctx->pt.x_inv(f, nullptr, ctx->W, ctx->stream);
-    ctx->pt.y_inv(f, ctx->W, ctx->stream);
+    ctx->pt.x_inv(f, -1, ctx->W, ctx->stream);
+    ctx->pt.y_inv(f, BUF_W, ctx->stream);
     ctx->pt.z_c2r(f, ctx->W, delta_dev, ctx->stream);
     LAUNCHED(ctx, 3);
   }
@@ -826,8 +830,8 @@ bps_status bps_fft_r2c(bps_ctx* ctx, const float* real_dev, float* spec_dev) {
   if (!ctx || !real_dev || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument");
   Fields f = fields(ctx);
   ctx->pt.z_r2c(f, real_dev, ctx->W, ctx->stream);
-  ctx->pt.y_fwd(f, ctx->W, ctx->stream);
-  ctx->pt.x_fwd(f, ctx->W, ctx->W, ctx->stream);
+  ctx->pt.y_fwd(f, BUF_W, ctx->stream);
+  ctx->pt.x_fwd(f, BUF_W, ctx->W, ctx->stream);
   LAUNCHED(ctx, 3);
   bps_status st = copy_spec_out(ctx, ctx->W, spec_dev);
   if (st != BPS_OK) return st;
@@ -840,8 +844,8 @@ bps_status bps_fft_c2r(bps_ctx* ctx, const float* spec_dev, float* real_dev) {
   bps_status st = copy_spec_in(ctx, spec_dev, ctx->W);
   if (st != BPS_OK) return st;
   Fields f = fields(ctx);
-  ctx->pt.x_inv(f, ctx->W, ctx->W, ctx->stream);
-  ctx->pt.y_inv(f, ctx->W, ctx->stream);
+  ctx->pt.x_inv(f, BUF_W, ctx->W, ctx->stream);
+  ctx->pt.y_inv(f, BUF_W, ctx->stream);
   ctx->pt.z_c2r(f, ctx->W, real_dev, ctx->stream);
   LAUNCHED(ctx, 3);
   CK(cudaStreamSynchronize(ctx->stream));
@@ -856,10 +860,10 @@ bps_status bps_gradient(bps_ctx* ctx, float* grad_dev, double* energies) {
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
   launch_move_begin(sa, s);   // per-bin tables of the current P and abar
-  ctx->pt.x_inv(f, nullptr, ctx->W, s);
-  ctx->pt.y_inv(f, ctx->W, s);
+  ctx->pt.x_inv(f, -1, ctx->W, s);
+  ctx->pt.y_inv(f, BUF_W, s);
   ctx->pt.z_grad(f, region_offset(ctx, RG_LIK0), s);
-  ctx->pt.y_fwd(f, ctx->W, s);
+  ctx->pt.y_fwd(f, BUF_W, s);
   ctx->pt.x_grad(f, ctx->W, region_offset(ctx, RG_GRAD), s);
   launch_reduce_to(sa, region_offset(ctx, RG_GRAD), ctx->pt.x_tiles, 1, 0.5 / (double)ctx->nv,
                    reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->ds) + DS_OFF(scratch)), s);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "bps_common.cuh"
+#include "bps_tma.cuh"
 
 namespace bps {
 
@@ -11,19 +12,19 @@ struct Fields;
 
 // Launchers of the field passes of one grid size (bps_passes.cu).
 struct PassTable {
-  int N, zp, x_tiles, z_tiles;
+  int N, zp, F, x_tiles, z_tiles;
   void (*x_init)(const Fields&, int region, cudaStream_t);
   void (*x_leap)(const Fields&, int first, cudaStream_t);
   void (*x_final)(const Fields&, int region, cudaStream_t);
-  void (*x_inv)(const Fields&, const float2* src, float2* dst, cudaStream_t);
-  void (*x_fwd)(const Fields&, const float2* src, float2* dst, cudaStream_t);
+  void (*x_inv)(const Fields&, int src_buf, float2* dst, cudaStream_t);   // src_buf -1: current state
+  void (*x_fwd)(const Fields&, int src_buf, float2* dst, cudaStream_t);   // dst NULL: current state
   void (*x_grad)(const Fields&, float2* dst, int region, cudaStream_t);
   void (*x_jinv)(const Fields&, cudaStream_t);
   void (*x_jgrad)(const Fields&, int region, cudaStream_t);
   void (*x_scale)(const Fields&, cudaStream_t);
   void (*x_binpow)(const Fields&, int region, cudaStream_t);
-  void (*y_fwd)(const Fields&, float2* buf, cudaStream_t);
-  void (*y_inv)(const Fields&, float2* buf, cudaStream_t);
+  void (*y_fwd)(const Fields&, int buf, cudaStream_t);
+  void (*y_inv)(const Fields&, int buf, cudaStream_t);
   void (*z_grad)(const Fields&, int region, cudaStream_t);
   void (*z_noise)(const Fields&, uint64_t seed, cudaStream_t);
   void (*z_r2c)(const Fields&, const float* rin, float2* dst, cudaStream_t);

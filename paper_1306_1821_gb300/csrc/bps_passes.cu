@@ -9,8 +9,9 @@
 //   y pass  : W = FFT_y(W)
 // so the force of Eq. Wiener_Posterior_force costs one 3D C2R and one 3D R2C
 // with the prior and the voxel-local likelihood fused into the passes.
-#include "bps_passes.cuh"
 #include "bps_internal.h"
+#include "bps_passes.cuh"
+#include "bps_tma.cuh"
 
 namespace bps {
 
@@ -33,7 +34,7 @@ enum ZMode { Z_GRAD = 0, Z_NOISE, Z_R2C, Z_C2R, Z_SUMS };
 __device__ __forceinline__ float2* dsel(const Fields& fp, int i) { return i ? fp.dh[1] : fp.dh[0]; }
 
 struct XArgs {
-  const float2* src;
+  int src_buf;   // staged input buffer (BUF_*), -1: the current state
   float2* dst;
   int first;
   int region;    // offset (doubles) of this launch's partial sums in Fields::part
@@ -48,9 +49,18 @@ struct ZArgs {
   uint64_t seed;
 };
 
+// ------------------------------------------------------------------ x pass helpers
+__device__ __forceinline__ const float2* buf_ptr(const Fields& fp, int b) {
+  return b == BUF_D0 ? fp.dh[0] : b == BUF_D1 ? fp.dh[1] : b == BUF_PH ? fp.ph : fp.W;
+}
+
+#ifndef BPS_XPASS_MIN_BLOCKS
+#define BPS_XPASS_MIN_BLOCKS 2
+#endif
+
 // ------------------------------------------------------------------ x pass
 template <int N, int MODE>
-__global__ void __launch_bounds__(Cfg<N>::NT, 2) k_xpass(Fields fp, XArgs xa) {
+__global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fields fp, XArgs xa) {
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT, NW = NT / 32;
   constexpr bool BINNED = (MODE == X_JGRAD || MODE == X_BINPOW);
@@ -116,7 +126,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, 2) k_xpass(Fields fp, XArgs xa) {
   // ---------------- modes that start from a spatial-x tile: forward transform
   if constexpr (MODE == X_INIT || MODE == X_LEAP || MODE == X_FINAL || MODE == X_FWD || MODE == X_GRAD ||
                 MODE == X_JGRAD) {
-    const float2* in = (MODE == X_INIT) ? fp.ph : (MODE == X_FWD) ? xa.src : fp.W;
+    const float2* in = (MODE == X_INIT) ? fp.ph : (MODE == X_FWD) ? buf_ptr(fp, xa.src_buf) : fp.W;
     // X_FWD with no destination writes the current state buffer
     if (ja < R1) {
 #pragma unroll
@@ -277,7 +287,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, 2) k_xpass(Fields fp, XArgs xa) {
 
   if constexpr (MODE == X_INV || MODE == X_JINV) {
     // X_INV with no source reads the current state buffer
-    const float2* src = (MODE == X_INV && xa.src) ? xa.src : dsel(fp, cur);
+    const float2* src = (MODE == X_INV && xa.src_buf >= 0) ? buf_ptr(fp, xa.src_buf) : dsel(fp, cur);
     if (act) {
 #pragma unroll
       for (int d = 0; d < R1; ++d) v[d] = src[colo + (long long)(jc + R2 * d) * T.rs];
@@ -349,66 +359,120 @@ __global__ void __launch_bounds__(Cfg<N>::NT, 2) k_xpass(Fields fp, XArgs xa) {
 
 // ------------------------------------------------------------------ y pass
 template <int N, int DIR>
-__global__ void __launch_bounds__(Cfg<N>::NT) k_ypass(Fields fp, float2* buf) {
+__global__ void __launch_bounds__(Cfg<N>::NT) k_ypass(Fields fp, int buf) {
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT;
   __shared__ float2 s_tw[N];
   __shared__ __align__(16) float2 s_ex[N * F];
   const int t = threadIdx.x;
-  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
-  __syncthreads();
   const Tile<N> T = tile_y<N>(blockIdx.x);
+  float2* data = const_cast<float2*>(buf_ptr(fp, buf));
   const int f = t % F, j = t / F;
   const long long colo = T.base + (long long)f * T.cs;
   float2 v[C::RMAX];
   if constexpr (DIR == FWD) {
     if (j < R1) {
 #pragma unroll
-      for (int b = 0; b < R2; ++b) v[b] = buf[colo + (long long)(j + R1 * b) * T.rs];
-    }
-    fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
-    if (j < R2) {
-#pragma unroll
-      for (int d = 0; d < R1; ++d) buf[colo + (long long)(j + R2 * d) * T.rs] = v[d];
+      for (int b = 0; b < R2; ++b) v[b] = data[colo + (long long)(j + R1 * b) * T.rs];
     }
   } else {
     if (j < R2) {
 #pragma unroll
-      for (int d = 0; d < R1; ++d) v[d] = buf[colo + (long long)(j + R2 * d) * T.rs];
+      for (int d = 0; d < R1; ++d) v[d] = data[colo + (long long)(j + R2 * d) * T.rs];
     }
+  }
+  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
+  __syncthreads();
+  if constexpr (DIR == FWD) {
+    fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
+    if (j < R2) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) data[colo + (long long)(j + R2 * d) * T.rs] = v[d];
+    }
+  } else {
     fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
     if (j < R1) {
 #pragma unroll
-      for (int b = 0; b < R2; ++b) buf[colo + (long long)(j + R1 * b) * T.rs] = v[b];
+      for (int b = 0; b < R2; ++b) data[colo + (long long)(j + R1 * b) * T.rs] = v[b];
     }
   }
 }
 
 // ------------------------------------------------------------------ z pass
 // 16 pairs of consecutive z lines per tile; line 2f is the real part and line
-// 2f+1 the imaginary part of one complex transform of length N.
+// 2f+1 the imaginary part of one complex transform of length N.  The lines of
+// the tile are contiguous in HBM and arrive by bulk copies.
+template <int N, int MODE>
+struct ZSmem {
+  using C = Cfg<N>;
+  static constexpr int LINES = 2 * C::LP;
+  static constexpr size_t BUF = (size_t)16 * (N + C::RMAX) * sizeof(float2);
+  static constexpr size_t AC = MODE == Z_GRAD ? (size_t)LINES * N * sizeof(float) : 0;
+  static constexpr size_t OFF_BUF = 0;
+  static constexpr size_t OFF_A = BUF;
+  static constexpr size_t OFF_C = OFF_A + AC;
+  static constexpr size_t OFF_TW = OFF_C + AC;
+  static constexpr size_t OFF_RED = OFF_TW + (size_t)N * sizeof(float2);
+  static constexpr size_t OFF_BAR = OFF_RED + 32 * sizeof(double);
+  static constexpr size_t BYTES = OFF_BAR + sizeof(uint64_t);
+  static_assert(BUF >= (size_t)LINES * C::ZP * sizeof(float2), "staging does not fit");
+  static_assert(BUF >= (size_t)LINES * N * sizeof(float), "staging does not fit");
+};
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
   using C = Cfg<N>;
+  using L = ZSmem<N, MODE>;
   constexpr int R1 = C::R1, R2 = C::R2, H = C::H, ZP = C::ZP, NTZ = C::NTZ;
-  constexpr int LINES = 2 * C::LP;
-  constexpr int BUF = 16 * (N + C::RMAX);
-  static_assert(BUF >= LINES * ZP, "staging does not fit");
-  __shared__ float2 s_tw[N];
-  __shared__ __align__(16) float2 s_buf[BUF];
-  __shared__ double s_red[32];
+  constexpr int LINES = L::LINES;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* s_buf = reinterpret_cast<float2*>(smem + L::OFF_BUF);
+  float* s_a = reinterpret_cast<float*>(smem + L::OFF_A);
+  float* s_c = reinterpret_cast<float*>(smem + L::OFF_C);
+  float2* s_tw = reinterpret_cast<float2*>(smem + L::OFF_TW);
+  double* s_red = reinterpret_cast<double*>(smem + L::OFF_RED);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   const int t = threadIdx.x;
   DevState* ds = fp.ds;
-  for (int i = t; i < N; i += NTZ) s_tw[i] = fp.tw[i];
   const long long L0 = (long long)blockIdx.x * LINES;
+  constexpr bool STAGED = MODE != Z_NOISE;
+  if constexpr (STAGED) {
+    if (t == 0) {
+      mbar_init(bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+      if constexpr (MODE == Z_R2C) {
+        constexpr uint32_t RB = LINES * N * sizeof(float);
+        mbar_expect_tx(bar, RB);
+        bulk_load(s_buf, za.rin + L0 * N, RB, bar);
+      } else {
+        const float2* src = (MODE == Z_C2R) ? za.src : fp.W;
+        constexpr uint32_t SB = LINES * ZP * sizeof(float2);
+        constexpr uint32_t AB = (uint32_t)L::AC;
+        mbar_expect_tx(bar, SB + 2 * AB);
+        bulk_load(s_buf, src + L0 * ZP, SB, bar);
+        if constexpr (MODE == Z_GRAD) {
+          bulk_load(s_a, fp.a + L0 * N, AB, bar);
+          bulk_load(s_c, fp.c + L0 * N, AB, bar);
+        }
+      }
+    }
+  }
+  for (int i = t; i < N; i += NTZ) s_tw[i] = fp.tw[i];
   float2 v[C::RMAX];
 
+  if constexpr (STAGED) {
+    bool ok = mbar_wait(bar, 0);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+      if (t == 0) atomicOr(&ds->status, ST_TIMEOUT);
+      return;
+    }
+  }
+
   if constexpr (MODE == Z_GRAD || MODE == Z_C2R || MODE == Z_SUMS) {
-    const float2* src = (MODE == Z_C2R) ? za.src : fp.W;
-    const float4* s4 = reinterpret_cast<const float4*>(src + L0 * ZP);
-    float4* b4 = reinterpret_cast<float4*>(s_buf);
-    for (int i = t; i < LINES * ZP / 2; i += NTZ) b4[i] = s4[i];
-    __syncthreads();
     {
       const int f = t / R2, a = t % R2;
       if (f < 16) {
@@ -449,12 +513,8 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
           sr[8 * q + 2 * j + 1] = rad * sn;
         }
       }
-    } else {
-      const float4* r4 = reinterpret_cast<const float4*>(za.rin + L0 * N);
-      float4* b4 = reinterpret_cast<float4*>(s_buf);
-      for (int i = t; i < LINES * N / 4; i += NTZ) b4[i] = r4[i];
+      __syncthreads();
     }
-    __syncthreads();
     const int f = t / R1, c = t % R1;
     if (f < 16) {
 #pragma unroll
@@ -513,20 +573,14 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
     // likelihood energy (1/2) sum (a delta^2 - 2 c delta)
     float e = 0.f;
     if (f < 16) {
-      float aa[C::RMAX], ca[C::RMAX], ab[C::RMAX], cb[C::RMAX];
+      const int ra = (2 * f) * N, rb = ra + N;
 #pragma unroll
       for (int d = 0; d < R2; ++d) {
         const int n = c + R1 * d;
-        aa[d] = fp.a[la + n];
-        ca[d] = fp.c[la + n];
-        ab[d] = fp.a[lb + n];
-        cb[d] = fp.c[lb + n];
-      }
-#pragma unroll
-      for (int d = 0; d < R2; ++d) {
+        const float aa = s_a[ra + n], ca = s_c[ra + n], ab = s_a[rb + n], cb = s_c[rb + n];
         const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
-        const float ga = fmaf(aa[d], da, -ca[d]), gb = fmaf(ab[d], db, -cb[d]);
-        e += da * (ga - ca[d]) + db * (gb - cb[d]);   // a d^2 - 2 c d
+        const float ga = fmaf(aa, da, -ca), gb = fmaf(ab, db, -cb);
+        e += da * (ga - ca) + db * (gb - cb);   // a d^2 - 2 c d
         v[d] = make_float2(ga, gb);
       }
     }
@@ -662,12 +716,20 @@ struct Launch {
     k_xpass<N, M><<<C::TILES, C::NT, 0, s>>>(fp, xa);
   }
   template <int D>
-  static void y(const Fields& fp, float2* buf, cudaStream_t s) {
+  static void y(const Fields& fp, int buf, cudaStream_t s) {
     k_ypass<N, D><<<C::TILES, C::NT, 0, s>>>(fp, buf);
   }
   template <int M>
   static void z(const Fields& fp, const ZArgs& za, cudaStream_t s) {
-    k_zpass<N, M><<<C::ZTILES, C::NTZ, 0, s>>>(fp, za);
+    k_zpass<N, M><<<C::ZTILES, C::NTZ, ZSmem<N, M>::BYTES, s>>>(fp, za);
+  }
+
+  template <int M>
+  static void zattr() {
+    cudaFuncSetAttribute(k_zpass<N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZSmem<N, M>::BYTES);
+  }
+  static void attrs() {
+    zattr<Z_GRAD>(); zattr<Z_NOISE>(); zattr<Z_R2C>(); zattr<Z_C2R>(); zattr<Z_SUMS>();
   }
 };
 
@@ -675,23 +737,25 @@ template <int N>
 static PassTable make_table() {
   using L = Launch<N>;
   using C = Cfg<N>;
+  L::attrs();
   PassTable T;
   T.N = N;
   T.zp = C::ZP;
+  T.F = C::F;
   T.x_tiles = C::TILES;
   T.z_tiles = C::ZTILES;
-  T.x_init = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_INIT>(f, XArgs{nullptr, nullptr, 0, region}, s); };
-  T.x_leap = [](const Fields& f, int first, cudaStream_t s) { L::template x<X_LEAP>(f, XArgs{nullptr, nullptr, first, -1}, s); };
-  T.x_final = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_FINAL>(f, XArgs{nullptr, nullptr, 0, region}, s); };
-  T.x_inv = [](const Fields& f, const float2* src, float2* dst, cudaStream_t s) { L::template x<X_INV>(f, XArgs{src, dst, 0, -1}, s); };
-  T.x_fwd = [](const Fields& f, const float2* src, float2* dst, cudaStream_t s) { L::template x<X_FWD>(f, XArgs{src, dst, 0, -1}, s); };
-  T.x_grad = [](const Fields& f, float2* dst, int region, cudaStream_t s) { L::template x<X_GRAD>(f, XArgs{nullptr, dst, 0, region}, s); };
-  T.x_jinv = [](const Fields& f, cudaStream_t s) { L::template x<X_JINV>(f, XArgs{nullptr, nullptr, 0, -1}, s); };
-  T.x_jgrad = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_JGRAD>(f, XArgs{nullptr, nullptr, 0, region}, s); };
-  T.x_scale = [](const Fields& f, cudaStream_t s) { L::template x<X_SCALE>(f, XArgs{nullptr, nullptr, 0, -1}, s); };
-  T.x_binpow = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_BINPOW>(f, XArgs{nullptr, nullptr, 0, region}, s); };
-  T.y_fwd = [](const Fields& f, float2* buf, cudaStream_t s) { L::template y<FWD>(f, buf, s); };
-  T.y_inv = [](const Fields& f, float2* buf, cudaStream_t s) { L::template y<INV>(f, buf, s); };
+  T.x_init = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_INIT>(f, XArgs{-1, nullptr, 0, region}, s); };
+  T.x_leap = [](const Fields& f, int first, cudaStream_t s) { L::template x<X_LEAP>(f, XArgs{-1, nullptr, first, -1}, s); };
+  T.x_final = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_FINAL>(f, XArgs{-1, nullptr, 0, region}, s); };
+  T.x_inv = [](const Fields& f, int src, float2* dst, cudaStream_t s) { L::template x<X_INV>(f, XArgs{src, dst, 0, -1}, s); };
+  T.x_fwd = [](const Fields& f, int src, float2* dst, cudaStream_t s) { L::template x<X_FWD>(f, XArgs{src, dst, 0, -1}, s); };
+  T.x_grad = [](const Fields& f, float2* dst, int region, cudaStream_t s) { L::template x<X_GRAD>(f, XArgs{-1, dst, 0, region}, s); };
+  T.x_jinv = [](const Fields& f, cudaStream_t s) { L::template x<X_JINV>(f, XArgs{-1, nullptr, 0, -1}, s); };
+  T.x_jgrad = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_JGRAD>(f, XArgs{-1, nullptr, 0, region}, s); };
+  T.x_scale = [](const Fields& f, cudaStream_t s) { L::template x<X_SCALE>(f, XArgs{-1, nullptr, 0, -1}, s); };
+  T.x_binpow = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_BINPOW>(f, XArgs{-1, nullptr, 0, region}, s); };
+  T.y_fwd = [](const Fields& f, int buf, cudaStream_t s) { L::template y<FWD>(f, buf, s); };
+  T.y_inv = [](const Fields& f, int buf, cudaStream_t s) { L::template y<INV>(f, buf, s); };
   T.z_grad = [](const Fields& f, int region, cudaStream_t s) { L::template z<Z_GRAD>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, s); };
   T.z_noise = [](const Fields& f, uint64_t seed, cudaStream_t s) { L::template z<Z_NOISE>(f, ZArgs{nullptr, f.ph, nullptr, nullptr, -1, seed}, s); };
   T.z_r2c = [](const Fields& f, const float* rin, float2* dst, cudaStream_t s) { L::template z<Z_R2C>(f, ZArgs{nullptr, dst, rin, nullptr, -1, 0}, s); };

@@ -35,6 +35,7 @@ struct Fields {
   const float2* tw;       // W_N^j = exp(-2 pi i j / N), j < N (FP64-rounded)
   float inv_nv;           // 1 / N^3
   int mass_mode;
+  int n_sm;               // streaming multiprocessors (grid of the persistent passes)
 };
 
 enum { MAP_COL = 0, MAP_ROW = 1 };

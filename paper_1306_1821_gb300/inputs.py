@@ -14,7 +14,9 @@ selection and Eisenstein-Hu spectrum are not available here:
     Eq. data_model with Poisson rather than Gaussian noise).
 
 Everything is drawn from numpy's PCG64 with a fixed seed, so each named
-workload is reproducible bit for bit.
+workload is reproducible bit for bit.  The step-size bounds eps_max are set for
+a density-move acceptance of roughly 0.8-0.9 at the true hyperparameters (the
+stable leapfrog step shrinks with the dimension, about as N_vox^(-1/4)).
 """
 from dataclasses import dataclass, field
 
@@ -56,13 +58,13 @@ SIX_B = [1.0, 1.1, 1.2, 1.35, 1.5, 1.65]
 WORKLOADS = {
     # 32^3, L = 500 Mpc/h, one subsample, 40% sky with linear radial fall-off
     "survey32": Workload("survey32", 32, 500.0, 16, [1.2], [5.0], 0.4, "linear",
-                         n_leapfrog=10, eps_max=0.35),
+                         n_leapfrog=10, eps_max=0.15),
     # 128^3, L = 750 Mpc/h, six luminosity subsamples, 25% sky, exp(-(r/350)^2)
     "survey128": Workload("survey128", 128, 750.0, 16, SIX_B, _six_nbar(), 0.25, "gauss",
-                          n_leapfrog=10, eps_max=0.3),
+                          n_leapfrog=10, eps_max=0.06),
     # 256^3, L = 1000 Mpc/h, six subsamples, 32 bins, 20 leapfrog steps, jump on
     "survey256": Workload("survey256", 256, 1000.0, 32, SIX_B, _six_nbar(), 0.25, "gauss",
-                          n_leapfrog=20, eps_max=0.25, jump=True, jump_leapfrog=10),
+                          n_leapfrog=20, eps_max=0.05, jump=True, jump_leapfrog=10),
 }
 
 
