@@ -347,6 +347,71 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched chains
+def run_batch(args):
+    """Aggregate throughput of 96 independent chains on 32^3 / 64^3 / 96^3 grids
+    (32 each), one CUDA graph replay per Gibbs iteration of the whole batch."""
+    import numpy as np
+    import torch
+
+    from paper_1306_1821_gb300 import bps, inputs
+    if not os.path.exists(bps.LIB_PATH):
+        from paper_1306_1821_gb300 import build as b
+        b.build()
+    bps.load()
+    wls = inputs.batch_workloads()
+    stream = torch.cuda.Stream()
+    cfg = bps.make_config(16, n_leapfrog=10, eps_max=0.1, jump=1, jump_leapfrog=5, jump_eps_max=0.05,
+                          fixed_bias_index=0, seed=1000)
+    batch = bps.bps_create_batch([w.N for w in wls], [w.box for w in wls], [w.n_sub for w in wls], cfg, stream)
+    t0 = time.time()
+    for j, wl in enumerate(wls):
+        delta, counts, R = inputs.make_survey(wl)
+        P, b, nbar = inputs.initial_state(wl)
+        with torch.cuda.stream(stream):
+            c_d = torch.from_numpy(counts).cuda()
+            r_d = torch.from_numpy(R).cuda()
+            d_d = torch.from_numpy(delta.astype(np.float32)).cuda()
+        stream.synchronize()
+        bps.bps_batch_set_chain(batch, j, c_d, r_d, d_d, P, b, nbar, 0)
+    setup_s = time.time() - t0
+    bps.bps_batch_gibbs_iterate(batch, max(args.warmup, 3))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = bps.bps_kernel_launches(batch)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rec = bps.bps_batch_gibbs_iterate(batch, args.steps, len(wls))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1000.0
+    launches = bps.bps_kernel_launches(batch) - l0
+    vox = sum(w.N ** 3 for w in wls)
+    acc = float(np.mean([rec[:, bps.bps_batch_record_slot(batch, j), 16 + 2 * w.n_sub + 1]
+                         for j, w in enumerate(wls)]))
+    line = {
+        "metric": "aggregate voxel-leapfrog steps/s, 96 batched chains",
+        "value": vox * cfg.n_leapfrog * args.steps / secs,
+        "unit": "voxel-leapfrogs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": 1000.0 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch96: 32 chains each of 32^3, 64^3, 96^3 (L = 500 N/32 Mpc/h), caps of "
+                               "20-60% sky, 1-4 subsamples, 16 bins, 10 leapfrog steps, jump on (5 steps); "
+                               "one CUDA graph replay per Gibbs iteration of all chains",
+                   "chains": len(wls), "voxels": vox},
+        "gibbs_iterations_per_s": len(wls) * args.steps / secs,
+        "hmc_acceptance": acc,
+        "gpu_launches": int(launches),
+        "setup_s": setup_s,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    bps.bps_destroy(batch)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,11 +419,14 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96"])
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch96":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -152,6 +152,34 @@ bps_status bps_jump(bps_ctx* ctx, bps_move_info* info);
  * n_iter * (n_bins + 2 n_sub + 2) doubles. */
 bps_status bps_gibbs_iterate(bps_ctx* ctx, int n_iter, double* chain_out);
 
+/* ---- batches of independent chains (many small surveys in one launch) ----
+ * A batch holds n_chains chains, each with its own grid (grid_n[j] in the set
+ * of bps_create), box (box_len[j]), subsamples (n_sub[j]) and Philox key
+ * cfg->seed + j; every other setting of cfg is shared.  Chains of equal grid
+ * size form one group whose field passes and scalar stages are single launches
+ * over all of the group's chains, and one Gibbs iteration of the whole batch is
+ * one CUDA graph replay.  The single-chain calls above do not accept a batch
+ * context; bps_destroy and bps_set_mass_scale do. */
+bps_status bps_create_batch(int n_chains, const int* grid_n, const double* box_len, const int* n_sub,
+                            const bps_config* cfg, void* cuda_stream, bps_ctx** out);
+
+/* Data and state of chain `chain` (as bps_set_data followed by bps_set_state). */
+bps_status bps_batch_set_chain(bps_ctx* batch, int chain, const int32_t* counts_dev, const float* R_dev,
+                               const float* delta_dev, const double* P, const double* b,
+                               const double* nbar, uint64_t iteration);
+
+/* State of chain `chain` (as bps_get_state). */
+bps_status bps_batch_get_chain(bps_ctx* batch, int chain, float* delta_dev, double* P, double* b,
+                               double* nbar, uint64_t* iteration);
+
+/* n_iter Gibbs iterations of every chain.  chain_out (host, may be NULL):
+ * [n_iter][n_chains][bps_batch_record_len] doubles; the record of chain j sits
+ * in slot bps_batch_record_slot(j) and holds n_bins P, n_sub(j) b, n_sub(j)
+ * Nbar, dH, accepted (the tail beyond a chain's record is unused). */
+bps_status bps_batch_gibbs_iterate(bps_ctx* batch, int n_iter, double* chain_out);
+int bps_batch_record_len(const bps_ctx* batch);
+int bps_batch_record_slot(const bps_ctx* batch, int chain);
+
 /* Per-bin multipliers s_m of the diagonal mass for mass_mode = 1 (a
  * preconditioner choice: the mass affects efficiency, not validity,
  * Sec. 4.1.2).  scales [n_mass_bins] host, 1 <= n_mass_bins <= 64, bins

@@ -64,6 +64,12 @@ _SIGS = {
     "bps_kernel_launches": ([_P], ctypes.c_uint64),
     "bps_profile": ([_P, ctypes.c_int], ctypes.c_int),
     "bps_profile_read": ([_P, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bps_create_batch": ([ctypes.c_int, _P, _P, _P, ctypes.POINTER(bps_config), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "bps_batch_set_chain": ([_P, ctypes.c_int, _P, _P, _P, _D, _D, _D, ctypes.c_uint64], ctypes.c_int),
+    "bps_batch_get_chain": ([_P, ctypes.c_int, _P, _D, _D, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bps_batch_gibbs_iterate": ([_P, ctypes.c_int, _D], ctypes.c_int),
+    "bps_batch_record_len": ([_P], ctypes.c_int),
+    "bps_batch_record_slot": ([_P, ctypes.c_int], ctypes.c_int),
     "bps_bin_power_noalloc": ([ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "bps_destroy": ([_P], None),
 }
@@ -251,6 +257,54 @@ def bps_bin_power_noalloc(grid_n, box_len, n_bins, spec, sigma, stream=None):
     """sigma (float64 CUDA tensor [n_bins]) <- k-bin power of spec, no device allocation."""
     _check(None, load().bps_bin_power_noalloc(int(grid_n), float(box_len), int(n_bins), _dptr(spec), _dptr(sigma),
                                               _stream_ptr(stream)))
+
+
+def bps_create_batch(grid_n, box_len, n_sub, cfg, stream=None):
+    lib = load()
+    g = np.ascontiguousarray(grid_n, dtype=np.int32)
+    bx = np.ascontiguousarray(box_len, dtype=np.float64)
+    ns = np.ascontiguousarray(n_sub, dtype=np.int32)
+    ctx = _P()
+    st = lib.bps_create_batch(int(g.size), g.ctypes.data_as(_P), bx.ctypes.data_as(_P), ns.ctypes.data_as(_P),
+                              ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def bps_batch_set_chain(ctx, chain, counts, R, delta, P, b, nbar, iteration=0):
+    _, pP = _darr(P)
+    _, pb = _darr(b)
+    _, pn = _darr(nbar)
+    _check(ctx, load().bps_batch_set_chain(ctx, int(chain), _dptr(counts), _dptr(R), _dptr(delta), pP, pb, pn,
+                                           int(iteration)))
+
+
+def bps_batch_get_chain(ctx, chain, delta=None, n_bins=64, n_sub=16):
+    P = np.zeros(n_bins)
+    b = np.zeros(n_sub)
+    nb = np.zeros(n_sub)
+    it = ctypes.c_uint64(0)
+    _check(ctx, load().bps_batch_get_chain(ctx, int(chain), _dptr(delta), P.ctypes.data_as(_D),
+                                           b.ctypes.data_as(_D), nb.ctypes.data_as(_D), ctypes.byref(it)))
+    return P, b, nb, it.value
+
+
+def bps_batch_record_len(ctx):
+    return int(load().bps_batch_record_len(ctx))
+
+
+def bps_batch_record_slot(ctx, chain):
+    return int(load().bps_batch_record_slot(ctx, int(chain)))
+
+
+def bps_batch_gibbs_iterate(ctx, n_iter, n_chains=None):
+    if n_chains is None:
+        _check(ctx, load().bps_batch_gibbs_iterate(ctx, int(n_iter), None))
+        return None
+    rl = bps_batch_record_len(ctx)
+    out = np.zeros(int(n_iter) * n_chains * rl)
+    _check(ctx, load().bps_batch_gibbs_iterate(ctx, int(n_iter), out.ctypes.data_as(_D)))
+    return out.reshape(int(n_iter), n_chains, rl)
 
 
 def bps_version():

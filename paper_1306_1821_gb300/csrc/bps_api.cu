@@ -1,11 +1,18 @@
 // Host side of the bps C ABI: context life cycle, data and state transfer, and
 // the launch sequences of the sampler's stages (the ABI is declared and
 // documented in include/bps.h).
+//
+// A context is a group of `batch` chains on one grid size: every chain has its
+// own buffers at fixed strides in shared arenas and its own DevState, and each
+// field pass or scalar stage is one launch over all chains (gridDim.y).  A
+// single-chain context is a group of one.  A batch context (bps_create_batch)
+// owns one group per distinct grid size.
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -15,8 +22,16 @@
 using namespace bps;
 
 struct bps_ctx {
-  int N = 0, n_sub = 0, zp = 0;
-  double box = 0, Vc = 0;
+  // ---- batch of groups (bps_create_batch) ----
+  bool is_batch = false;
+  std::vector<bps_ctx*> groups;
+  std::vector<std::pair<int, int>> chain_map;   // chain -> (group, index in group)
+  int rec_len_all = 0;
+  // ---- group of chains on one grid ----
+  int N = 0, batch = 1, max_sub = 0, zp = 0;
+  std::vector<int> nsub;                        // per chain
+  std::vector<double> box;                      // per chain
+  std::vector<int> chain_id;                    // per chain: slot in the batch record
   bps_config cfg{};
   cudaStream_t stream = nullptr;
   PassTable pt{};
@@ -32,15 +47,21 @@ struct bps_ctx {
   float2* tw = nullptr;
   double* part = nullptr;
   int part_stride = 0;
+  long long part_cstride = 0;
   DevState* ds = nullptr;
   double* chain_dev = nullptr;
   int chain_cap = 0;
   double* host_buf = nullptr;   // pinned staging for small reads
   int n_mass = 0;
-  bool have_data = false;
+  std::vector<char> have_data;
   int rebuild_blocks = 0;
   int n_sm = 0;
   uint64_t launches = 0;
+  // CUDA graph of one Gibbs iteration (captured on first use)
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
+  bool graph_jump = false;
+  uint64_t graph_launches = 0;   // kernels in one replay of the graph
   // leapfrog kernel timing (bps_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev[4];
@@ -54,9 +75,8 @@ namespace {
 
 std::string g_err;
 
-// partial-sum regions (offsets in doubles into ctx->part)
+// partial-sum regions (offsets in doubles into one chain's part of ctx->part)
 enum Region { RG_INIT = 0, RG_LIK0, RG_FINAL, RG_LIK1, RG_BIN, RG_SUMS, RG_RB, RG_JGRAD, RG_JLIK, RG_GRAD, RG_COUNT };
-// quantities per region
 int region_width(Region r) {
   switch (r) {
     case RG_INIT: case RG_FINAL: return 2;
@@ -110,7 +130,7 @@ Fields fields(bps_ctx* c) {
   f.c = c->c;
   f.cnt = c->cnt;
   f.R = c->R;
-  f.n_sub = c->n_sub;
+  f.n_sub = c->max_sub;
   f.ds = c->ds;
   f.part = c->part;
   f.part_stride = c->part_stride;
@@ -118,24 +138,36 @@ Fields fields(bps_ctx* c) {
   f.inv_nv = (float)(1.0 / (double)c->nv);
   f.mass_mode = c->cfg.mass_mode;
   f.n_sm = c->n_sm;
+  f.spec_stride = (long long)c->n_spec;
+  f.real_stride = c->nv;
+  f.data_stride = (long long)c->max_sub * c->nv;
+  f.part_cstride = c->part_cstride;
   return f;
 }
+
+Fields fields_at(bps_ctx* c, int ch) { return at_chain(fields(c), ch); }
 
 ScalarArgs scalars(bps_ctx* c) {
   ScalarArgs a;
   a.ds = c->ds;
   a.part = c->part;
   a.stride = c->part_stride;
+  a.cstride = c->part_cstride;
   a.n_bins = c->cfg.n_bins;
-  a.n_sub = c->n_sub;
+  a.max_sub = c->max_sub;
   a.n_mass = c->n_mass;
-  a.Vc = c->Vc;
   a.inv_nv = 1.0 / (double)c->nv;
   a.alpha = c->cfg.alpha;
   a.eps_max = c->cfg.eps_max;
   a.jeps_max = c->cfg.jump_eps_max;
-  a.seed = c->cfg.seed;
   a.fixed_bias = c->cfg.fixed_bias_index;
+  return a;
+}
+
+ScalarArgs scalars_at(bps_ctx* c, int ch) {
+  ScalarArgs a = scalars(c);
+  a.ds += ch;
+  a.part += ch * a.cstride;
   return a;
 }
 
@@ -184,45 +216,43 @@ bool bin_tables(int N, int nb, int* thr, double* nmodes) {
   return true;
 }
 
-bps_status ds_write_bytes(bps_ctx* ctx, size_t off, const void* src, size_t n) {
-  CK(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->ds) + off, src, n, cudaMemcpyHostToDevice, ctx->stream));
+#define DS_OFF(member) offsetof(DevState, member)
+
+char* ds_addr(bps_ctx* ctx, int ch, size_t off) { return reinterpret_cast<char*>(ctx->ds + ch) + off; }
+
+bps_status ds_write_bytes(bps_ctx* ctx, int ch, size_t off, const void* src, size_t n) {
+  CK(cudaMemcpyAsync(ds_addr(ctx, ch, off), src, n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return BPS_OK;
 }
 
-bps_status ds_read_bytes(bps_ctx* ctx, size_t off, void* dst, size_t n) {
-  CK(cudaMemcpyAsync(ctx->host_buf, reinterpret_cast<char*>(ctx->ds) + off, n, cudaMemcpyDeviceToHost, ctx->stream));
+bps_status ds_read_bytes(bps_ctx* ctx, int ch, size_t off, void* dst, size_t n) {
+  CK(cudaMemcpyAsync(ctx->host_buf, ds_addr(ctx, ch, off), n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   std::memcpy(dst, ctx->host_buf, n);
   return BPS_OK;
 }
 
-#define DS_OFF(member) offsetof(DevState, member)
-
+// status words of all chains; cleared after reading
 bps_status check_status(bps_ctx* ctx) {
-  int st = 0;
-  bps_status s = ds_read_bytes(ctx, DS_OFF(status), &st, sizeof(int));
-  if (s != BPS_OK) return s;
-  if (st != 0) {
-    int zero = 0;
-    ds_write_bytes(ctx, DS_OFF(status), &zero, sizeof(int));
-    if (st & ST_TIMEOUT) return fail(ctx, BPS_ETIMEOUT, "a tile copy did not complete within the wait limit");
-    if (st & ST_NONFINITE) return fail(ctx, BPS_ENUMERIC, "non-finite energy difference; move rejected");
-    return fail(ctx, BPS_ENUMERIC, "a scalar draw failed (no acceptance within the attempt bound or a non-positive sum)");
+  int any = 0;
+  for (int ch = 0; ch < ctx->batch; ++ch) {
+    int st = 0;
+    bps_status s = ds_read_bytes(ctx, ch, DS_OFF(status), &st, sizeof(int));
+    if (s != BPS_OK) return s;
+    if (st != 0) {
+      int zero = 0;
+      ds_write_bytes(ctx, ch, DS_OFF(status), &zero, sizeof(int));
+      any |= st;
+    }
   }
+  if (any & ST_TIMEOUT) return fail(ctx, BPS_ETIMEOUT, "a tile copy did not complete within the wait limit");
+  if (any & ST_NONFINITE) return fail(ctx, BPS_ENUMERIC, "non-finite energy difference; move rejected");
+  if (any) return fail(ctx, BPS_ENUMERIC, "a scalar draw failed (no acceptance within the attempt bound or a non-positive sum)");
   return BPS_OK;
 }
 
-// ------------------------------------------------------------------ stages
-bps_status rebuild(bps_ctx* ctx) {
-  Fields f = fields(ctx);
-  ScalarArgs sa = scalars(ctx);
-  launch_rebuild(f, ctx->nv, region_offset(ctx, RG_RB), ctx->rebuild_blocks, ctx->stream);
-  launch_abar(sa, region_offset(ctx, RG_RB), ctx->rebuild_blocks, ctx->stream);
-  LAUNCHED(ctx, 2);
-  return BPS_OK;
-}
-
+// ------------------------------------------------------------------ profiling
 constexpr size_t PROF_CAP = 8192;   // event pairs per kernel kind before folding
 
 void prof_fold(bps_ctx* ctx) {
@@ -251,40 +281,54 @@ void prof_mark(bps_ctx* ctx, int k) {
   cudaEventRecord(ctx->ev[k][ctx->ev_used[k]++], ctx->stream);
 }
 
-// force of the current state into W (Fourier), likelihood energy partials in `lik_region`
+// ------------------------------------------------------------------ stages (all chains of a group)
+bps_status rebuild_chain(bps_ctx* ctx, int ch) {
+  launch_rebuild(fields_at(ctx, ch), ctx->nv, region_offset(ctx, RG_RB), ctx->rebuild_blocks, 1, ctx->stream);
+  launch_abar(scalars_at(ctx, ch), region_offset(ctx, RG_RB), ctx->rebuild_blocks, 1, ctx->stream);
+  LAUNCHED(ctx, 2);
+  return BPS_OK;
+}
+
+bps_status rebuild_all(bps_ctx* ctx) {
+  launch_rebuild(fields(ctx), ctx->nv, region_offset(ctx, RG_RB), ctx->rebuild_blocks, ctx->batch, ctx->stream);
+  launch_abar(scalars(ctx), region_offset(ctx, RG_RB), ctx->rebuild_blocks, ctx->batch, ctx->stream);
+  LAUNCHED(ctx, 2);
+  return BPS_OK;
+}
+
 bps_status hmc_move(bps_ctx* ctx, bool advance) {
   Fields f = fields(ctx);
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
   const PassTable& P = ctx->pt;
-  const int L = ctx->cfg.n_leapfrog;
-  launch_move_begin(sa, s);
-  P.z_noise(f, ctx->cfg.seed, s);
-  P.y_fwd(f, BUF_PH, s);
-  P.x_init(f, region_offset(ctx, RG_INIT), s);
-  P.y_inv(f, BUF_W, s);
-  P.z_grad(f, region_offset(ctx, RG_LIK0), s);
-  P.y_fwd(f, BUF_W, s);
+  const int L = ctx->cfg.n_leapfrog, B = ctx->batch;
+  launch_move_begin(sa, B, s);
+  P.z_noise(f, B, s);
+  P.y_fwd(f, BUF_PH, B, s);
+  P.x_init(f, region_offset(ctx, RG_INIT), B, s);
+  P.y_inv(f, BUF_W, B, s);
+  P.z_grad(f, region_offset(ctx, RG_LIK0), B, s);
+  P.y_fwd(f, BUF_W, B, s);
   for (int st = 1; st <= L; ++st) {
     prof_mark(ctx, 0);
-    P.x_leap(f, st == 1 ? 1 : 0, s);
+    P.x_leap(f, st == 1 ? 1 : 0, B, s);
     prof_mark(ctx, 0);
     prof_mark(ctx, 1);
-    P.y_inv(f, BUF_W, s);
+    P.y_inv(f, BUF_W, B, s);
     prof_mark(ctx, 1);
     prof_mark(ctx, 2);
-    P.z_grad(f, st == L ? region_offset(ctx, RG_LIK1) : -1, s);
+    P.z_grad(f, st == L ? region_offset(ctx, RG_LIK1) : -1, B, s);
     prof_mark(ctx, 2);
     prof_mark(ctx, 3);
-    P.y_fwd(f, BUF_W, s);
+    P.y_fwd(f, BUF_W, B, s);
     prof_mark(ctx, 3);
   }
-  P.x_final(f, region_offset(ctx, RG_FINAL), s);
+  P.x_final(f, region_offset(ctx, RG_FINAL), B, s);
   launch_move_end(sa, region_offset(ctx, RG_INIT), region_offset(ctx, RG_LIK0), region_offset(ctx, RG_FINAL),
-                  region_offset(ctx, RG_LIK1), P.x_tiles, P.z_tiles, s);
+                  region_offset(ctx, RG_LIK1), P.x_tiles, P.z_tiles, B, s);
   int n = 9 + 4 * L;
   if (advance) {
-    launch_advance(ctx->ds, s);
+    launch_advance(ctx->ds, B, s);
     ++n;
   }
   LAUNCHED(ctx, n);
@@ -294,11 +338,12 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
 bps_status power_stage(bps_ctx* ctx, bool draw, bool advance) {
   Fields f = fields(ctx);
   ScalarArgs sa = scalars(ctx);
-  ctx->pt.x_binpow(f, region_offset(ctx, RG_BIN), ctx->stream);
-  launch_power(sa, region_offset(ctx, RG_BIN), ctx->pt.x_tiles, draw ? 1 : 0, ctx->stream);
+  const int B = ctx->batch;
+  ctx->pt.x_binpow(f, region_offset(ctx, RG_BIN), B, ctx->stream);
+  launch_power(sa, region_offset(ctx, RG_BIN), ctx->pt.x_tiles, draw ? 1 : 0, B, ctx->stream);
   int n = 2;
   if (advance) {
-    launch_advance(ctx->ds, ctx->stream);
+    launch_advance(ctx->ds, B, ctx->stream);
     ++n;
   }
   LAUNCHED(ctx, n);
@@ -309,16 +354,17 @@ bps_status bias_stage(bps_ctx* ctx, bool advance) {
   Fields f = fields(ctx);
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
+  const int B = ctx->batch;
   // delta = C2R(delta_hat) (x and y inverse into W), the per-subsample sums in the z pass
-  ctx->pt.x_inv(f, -1, ctx->W, s);
-  ctx->pt.y_inv(f, BUF_W, s);
-  ctx->pt.z_sums(f, region_offset(ctx, RG_SUMS), s);
-  launch_bias_nbar(sa, region_offset(ctx, RG_SUMS), ctx->pt.z_tiles, s);
+  ctx->pt.x_inv(f, -1, nullptr, B, s);
+  ctx->pt.y_inv(f, BUF_W, B, s);
+  ctx->pt.z_sums(f, region_offset(ctx, RG_SUMS), B, s);
+  launch_bias_nbar(sa, region_offset(ctx, RG_SUMS), ctx->pt.z_tiles, B, s);
   LAUNCHED(ctx, 4);
-  bps_status st = rebuild(ctx);
+  bps_status st = rebuild_all(ctx);
   if (st != BPS_OK) return st;
   if (advance) {
-    launch_advance(ctx->ds, s);
+    launch_advance(ctx->ds, B, s);
     LAUNCHED(ctx, 1);
   }
   return BPS_OK;
@@ -330,12 +376,13 @@ bps_status jump_gradient(bps_ctx* ctx) {
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
   const PassTable& P = ctx->pt;
-  P.x_jinv(f, s);
-  P.y_inv(f, BUF_W, s);
-  P.z_grad(f, region_offset(ctx, RG_JLIK), s);
-  P.y_fwd(f, BUF_W, s);
-  P.x_jgrad(f, region_offset(ctx, RG_JGRAD), s);
-  launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), P.z_tiles, s);
+  const int B = ctx->batch;
+  P.x_jinv(f, B, s);
+  P.y_inv(f, BUF_W, B, s);
+  P.z_grad(f, region_offset(ctx, RG_JLIK), B, s);
+  P.y_fwd(f, BUF_W, B, s);
+  P.x_jgrad(f, region_offset(ctx, RG_JGRAD), B, s);
+  launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), P.z_tiles, B, s);
   LAUNCHED(ctx, 6);
   return BPS_OK;
 }
@@ -343,34 +390,52 @@ bps_status jump_gradient(bps_ctx* ctx) {
 bps_status jump_stage(bps_ctx* ctx, bool advance) {
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
+  const int B = ctx->batch;
   bps_status st = power_stage(ctx, false, false);   // sigma of the current field (mass of the jump)
   if (st != BPS_OK) return st;
-  launch_jump_begin(sa, s);
+  launch_jump_begin(sa, B, s);
   LAUNCHED(ctx, 1);
   const int L = ctx->cfg.jump_leapfrog;
   st = jump_gradient(ctx);
   if (st != BPS_OK) return st;
-  launch_jump_update(sa, J_FIRST, s);
+  launch_jump_update(sa, J_FIRST, B, s);
   LAUNCHED(ctx, 1);
   for (int k = 0; k < L; ++k) {
     st = jump_gradient(ctx);
     if (st != BPS_OK) return st;
-    launch_jump_update(sa, k == L - 1 ? J_LAST : J_MID, s);
+    launch_jump_update(sa, k == L - 1 ? J_LAST : J_MID, B, s);
     LAUNCHED(ctx, 1);
   }
   Fields f = fields(ctx);
-  ctx->pt.x_scale(f, s);   // delta_k <- sqrt(P'/P) delta_k if accepted (Eq. det_trans)
+  ctx->pt.x_scale(f, B, s);   // delta_k <- sqrt(P'/P) delta_k if accepted (Eq. det_trans)
   LAUNCHED(ctx, 1);
   if (advance) {
-    launch_advance(ctx->ds, s);
+    launch_advance(ctx->ds, B, s);
     LAUNCHED(ctx, 1);
   }
   return BPS_OK;
 }
 
+// One Gibbs iteration of every chain of the group, recording each chain's
+// sample into `rec` (slot DevState::rec_idx, layout [slot][chain][rec_len]).
+bps_status gibbs_once(bps_ctx* ctx, double* rec, int rec_len, long long iter_stride, bool jump) {
+  bps_status st = hmc_move(ctx, false);
+  if (st == BPS_OK) st = power_stage(ctx, true, false);
+  if (st == BPS_OK && jump) st = jump_stage(ctx, false);
+  if (st == BPS_OK) st = bias_stage(ctx, false);
+  if (st != BPS_OK) return st;
+  launch_record(scalars(ctx), rec, rec_len, iter_stride, ctx->chain_id.empty() ? 0 : ctx->chain_id[0], ctx->batch,
+                ctx->stream);
+  launch_advance(ctx->ds, ctx->batch, ctx->stream);
+  LAUNCHED(ctx, 2);
+  return BPS_OK;
+}
+
 bps_status need_data(bps_ctx* ctx) {
   if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
-  if (!ctx->have_data) return fail(ctx, BPS_ESTATE, "bps_set_data has not been called");
+  if (ctx->is_batch) return fail(ctx, BPS_EINVAL, "a batch context takes the bps_batch_* calls");
+  for (int ch = 0; ch < ctx->batch; ++ch)
+    if (!ctx->have_data[ch]) return fail(ctx, BPS_ESTATE, "bps_set_data has not been called");
   return BPS_OK;
 }
 
@@ -388,13 +453,27 @@ bps_status copy_spec_in(bps_ctx* ctx, const float* src, float2* dst) {
   return BPS_OK;
 }
 
-int current_buffer(bps_ctx* ctx, bps_status* st) {
+int current_buffer(bps_ctx* ctx, int ch, bps_status* st) {
   int cur = 0;
-  *st = ds_read_bytes(ctx, DS_OFF(cur), &cur, sizeof(int));
+  *st = ds_read_bytes(ctx, ch, DS_OFF(cur), &cur, sizeof(int));
   return cur;
 }
 
+float2* state_buffer(bps_ctx* ctx, int ch, int cur) { return ctx->dh[cur] + (size_t)ch * ctx->n_spec; }
+
+void drop_graph(bps_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+void free_streams(bps_ctx* c) {
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
+}
+
 void free_all(bps_ctx* c) {
+  drop_graph(c);
+  free_streams(c);
   for (int k = 0; k < 4; ++k)
     for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);
   cudaFree(c->dh[0]);
@@ -412,6 +491,319 @@ void free_all(bps_ctx* c) {
   if (c->host_buf) cudaFreeHost(c->host_buf);
 }
 
+// ------------------------------------------------------------------ group construction
+bps_status check_config(const bps_config* cfg, int min_sub) {
+  if (cfg->n_bins < 1 || cfg->n_bins > MAXB) return fail(nullptr, BPS_EINVAL, "n_bins must be in 1..64");
+  if (cfg->n_leapfrog < 1 || !(cfg->eps_max > 0.0)) return fail(nullptr, BPS_EINVAL, "bad leapfrog settings");
+  if (cfg->jump && (cfg->jump_leapfrog < 1 || !(cfg->jump_eps_max > 0.0)))
+    return fail(nullptr, BPS_EINVAL, "bad jump settings");
+  if (cfg->fixed_bias_index >= min_sub) return fail(nullptr, BPS_EINVAL, "fixed_bias_index out of range");
+  if (cfg->mass_mode != 0 && cfg->mass_mode != 1) return fail(nullptr, BPS_EINVAL, "mass_mode must be 0 or 1");
+  return BPS_OK;
+}
+
+// One group: chains j with box[j], nsub[j], seeds[j]; ids[j] = record slot (empty: a single chain).
+bps_status create_group(int grid_n, const std::vector<double>& box, const std::vector<int>& nsub,
+                        const std::vector<uint64_t>& seeds, const std::vector<int>& ids, const bps_config* cfg,
+                        cudaStream_t stream, bps_ctx** out) {
+  *out = nullptr;
+  PassTable pt;
+  if (!pass_table(grid_n, &pt)) return fail(nullptr, BPS_EINVAL, "unsupported grid size (8,16,32,64,96,128,256)");
+  const int B = (int)box.size();
+  int max_sub = 0;
+  for (int j = 0; j < B; ++j) {
+    if (!(box[j] > 0.0) || !std::isfinite(box[j])) return fail(nullptr, BPS_EINVAL, "box length must be positive");
+    if (nsub[j] < 1 || nsub[j] > MAXS) return fail(nullptr, BPS_EINVAL, "n_sub must be in 1..16");
+    max_sub = std::max(max_sub, nsub[j]);
+  }
+  bps_status cs = check_config(cfg, *std::min_element(nsub.begin(), nsub.end()));
+  if (cs != BPS_OK) return cs;
+
+  DevState h;
+  std::memset(&h, 0, sizeof(h));
+  if (!bin_tables(grid_n, cfg->n_bins, h.thr, h.nmodes))
+    return fail(nullptr, BPS_EINVAL, "a power-spectrum bin holds no mode; use fewer bins");
+  bin_tables(grid_n, cfg->n_bins, h.mthr, nullptr);
+  for (int m = 0; m < MAXB; ++m) {
+    h.P[m] = 1.0;
+    h.P_ref[m] = 1.0;
+    h.mass_scale[m] = 1.0;
+    h.js[m] = 1.f;
+  }
+  for (int l = 0; l < MAXS; ++l) {
+    h.b[l] = 1.0;
+    h.nbar[l] = 1.0;
+  }
+
+  bps_ctx* ctx = new bps_ctx();
+  ctx->N = grid_n;
+  ctx->batch = B;
+  ctx->max_sub = max_sub;
+  ctx->nsub = nsub;
+  ctx->box = box;
+  ctx->chain_id = ids;
+  ctx->cfg = *cfg;
+  ctx->stream = stream;
+  ctx->pt = pt;
+  ctx->zp = pt.zp;
+  ctx->nv = (long long)grid_n * grid_n * grid_n;
+  ctx->n_spec = (size_t)grid_n * grid_n * pt.zp;
+  ctx->n_mass = cfg->n_bins;
+  ctx->chain_cap = ids.empty() ? 1024 : 0;
+  ctx->have_data.assign(B, 0);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  ctx->n_sm = sms > 0 ? sms : 148;
+  // the voxel kernels of a batch run B chains side by side: fewer blocks each
+  ctx->rebuild_blocks = std::max(1, std::min(4 * ctx->n_sm / B + 1, (int)(ctx->nv / 1024) + 1));
+  ctx->part_stride = std::max(std::max(pt.x_tiles, pt.z_tiles), ctx->rebuild_blocks);
+  ctx->part_cstride = (long long)region_total() * ctx->part_stride;
+
+  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+  const size_t sb = ctx->n_spec * sizeof(float2) * B, rb = (size_t)ctx->nv * sizeof(float) * B;
+  const int rec_len = cfg->n_bins + 2 * max_sub + 2;
+  bool ok = alloc((void**)&ctx->dh[0], sb) && alloc((void**)&ctx->dh[1], sb) && alloc((void**)&ctx->ph, sb) &&
+            alloc((void**)&ctx->W, sb) && alloc((void**)&ctx->a, rb) && alloc((void**)&ctx->c, rb) &&
+            alloc((void**)&ctx->tw, grid_n * sizeof(float2)) &&
+            alloc((void**)&ctx->part, (size_t)ctx->part_cstride * B * sizeof(double)) &&
+            alloc((void**)&ctx->ds, sizeof(DevState) * B) &&
+            (!ids.empty() || alloc((void**)&ctx->chain_dev, (size_t)ctx->chain_cap * rec_len * sizeof(double))) &&
+            cudaMallocHost((void**)&ctx->host_buf, 64 * 1024) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(ctx);
+    delete ctx;
+    return fail(nullptr, BPS_ENOMEM, "device allocation failed");
+  }
+  // twiddles W_N^j = exp(-2 pi i j / N), FP64 rounded to FP32
+  std::vector<float2> tw(grid_n);
+  for (int j = 0; j < grid_n; ++j) {
+    const double ang = -2.0 * M_PI * (double)j / (double)grid_n;
+    tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  std::vector<DevState> hs(B, h);
+  for (int j = 0; j < B; ++j) {
+    hs[j].vc = std::pow(box[j] / grid_n, 3);
+    hs[j].seed = seeds[j];
+    hs[j].nsub = nsub[j];
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->tw, tw.data(), grid_n * sizeof(float2), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ds, hs.data(), sizeof(DevState) * B, cudaMemcpyHostToDevice, stream);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(ctx->dh[i], 0, sb, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ph, 0, sb, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->W, 0, sb, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->a, 0, rb, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->c, 0, rb, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("initialisation failed: ") + cudaGetErrorString(e);
+    free_all(ctx);
+    delete ctx;
+    return fail(nullptr, BPS_ECUDA, msg);
+  }
+  *out = ctx;
+  return BPS_OK;
+}
+
+// ------------------------------------------------------------------ per-chain operations
+bps_status set_data_chain(bps_ctx* ctx, int ch, const int32_t* counts, const float* R, bool host) {
+  if (!counts || !R) return fail(ctx, BPS_EINVAL, "null argument");
+  cudaStream_t s = ctx->stream;
+  const int ns = ctx->nsub[ch];
+  if (!ctx->cnt) {
+    const size_t total = (size_t)ctx->max_sub * ctx->nv * ctx->batch;
+    if (cudaMalloc((void**)&ctx->cnt, total * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->R, total * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ctx->cnt);
+      cudaFree(ctx->R);
+      ctx->cnt = nullptr;
+      ctx->R = nullptr;
+      return fail(ctx, BPS_ENOMEM, "device allocation of the survey data failed");
+    }
+    CK(cudaMemsetAsync(ctx->cnt, 0, total * sizeof(uint16_t), s));
+    CK(cudaMemsetAsync(ctx->R, 0, total * sizeof(float), s));
+  }
+  Fields f = fields_at(ctx, ch);
+  uint16_t* cnt_ch = const_cast<uint16_t*>(f.cnt);
+  float* R_ch = const_cast<float*>(f.R);
+  int32_t* ctmp = nullptr;
+  float* rtmp = nullptr;
+  if (host) {
+    // stage through this chain's spectrum work buffers (each at least N^3 * 8 bytes)
+    ctmp = reinterpret_cast<int32_t*>(f.ph);
+    rtmp = reinterpret_cast<float*>(f.W);
+  }
+  const int blocks = ctx->rebuild_blocks;
+  double* part = ctx->part + ch * ctx->part_cstride;
+  std::vector<double> hp(4 * (size_t)blocks);
+  std::vector<double> sR(ns), sB(ns), no(ns);
+  double bad = 0.0;
+  for (int l = 0; l < ns; ++l) {
+    const int32_t* cl = counts + (size_t)l * ctx->nv;
+    const float* rl = R + (size_t)l * ctx->nv;
+    if (host) {
+      CK(cudaMemcpyAsync(ctmp, cl, ctx->nv * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(rtmp, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, s));
+      cl = ctmp;
+      rl = rtmp;
+    }
+    launch_data(cl, rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv, ctx->nv, part, blocks, blocks, s);
+    LAUNCHED(ctx, 1);
+    CK(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double v[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q)
+      for (int b = 0; b < blocks; ++b) v[q] += hp[(size_t)q * blocks + b];
+    sR[l] = v[0];
+    sB[l] = v[1];
+    no[l] = v[2];
+    bad += v[3];
+  }
+  if (host) {
+    CK(cudaMemsetAsync(f.ph, 0, ctx->n_spec * sizeof(float2), s));
+    CK(cudaMemsetAsync(f.W, 0, ctx->n_spec * sizeof(float2), s));
+  }
+  if (bad > 0.0) {
+    ctx->have_data[ch] = 0;
+    return fail(ctx, BPS_EINVAL, "invalid survey data: R < 0 or non-finite, a count outside 0..65535, or a count > 0 where R = 0");
+  }
+  for (int l = 0; l < ns; ++l)
+    if (!(no[l] > 0.0)) return fail(ctx, BPS_EINVAL, "a subsample has no observed voxel (R > 0)");
+  bps_status st = ds_write_bytes(ctx, ch, DS_OFF(sumR), sR.data(), ns * sizeof(double));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(sumB), sB.data(), ns * sizeof(double));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(nobs), no.data(), ns * sizeof(double));
+  if (st != BPS_OK) return st;
+  ctx->have_data[ch] = 1;
+  st = rebuild_chain(ctx, ch);
+  if (st != BPS_OK) return st;
+  CK(cudaStreamSynchronize(s));
+  return BPS_OK;
+}
+
+bps_status set_state_chain(bps_ctx* ctx, int ch, const float* delta_dev, const double* P, const double* b,
+                           const double* nbar, uint64_t iteration) {
+  if (!P || !b || !nbar) return fail(ctx, BPS_EINVAL, "null argument");
+  const int nb = ctx->cfg.n_bins, ns = ctx->nsub[ch];
+  for (int m = 0; m < nb; ++m)
+    if (!(P[m] > 0.0) || !std::isfinite(P[m])) return fail(ctx, BPS_EINVAL, "P must be positive and finite");
+  for (int l = 0; l < ns; ++l)
+    if (!std::isfinite(b[l]) || !(nbar[l] > 0.0) || !std::isfinite(nbar[l]))
+      return fail(ctx, BPS_EINVAL, "b must be finite and nbar positive");
+  bps_status st = ds_write_bytes(ctx, ch, DS_OFF(P), P, nb * sizeof(double));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(P_ref), P, nb * sizeof(double));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(b), b, ns * sizeof(double));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(nbar), nbar, ns * sizeof(double));
+  unsigned long long it = iteration;
+  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(iteration), &it, sizeof(it));
+  if (st != BPS_OK) return st;
+  Fields f = fields_at(ctx, ch);
+  if (delta_dev) {
+    ctx->pt.z_r2c(f, delta_dev, f.W, ctx->stream);
+    ctx->pt.y_fwd(f, BUF_W, 1, ctx->stream);
+    ctx->pt.x_fwd(f, BUF_W, nullptr, 1, ctx->stream);
+    LAUNCHED(ctx, 3);
+    int cur = current_buffer(ctx, ch, &st);
+    if (st != BPS_OK) return st;
+    launch_zero_dc(state_buffer(ctx, ch, cur), ctx->stream);
+    LAUNCHED(ctx, 1);
+  }
+  if (ctx->have_data[ch]) {
+    st = rebuild_chain(ctx, ch);
+    if (st != BPS_OK) return st;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BPS_OK;
+}
+
+bps_status get_state_chain(bps_ctx* ctx, int ch, float* delta_dev, double* P, double* b, double* nbar,
+                           uint64_t* iteration) {
+  bps_status st = BPS_OK;
+  if (delta_dev) {
+    Fields f = fields_at(ctx, ch);
+    ctx->pt.x_inv(f, -1, f.W, 1, ctx->stream);
+    ctx->pt.y_inv(f, BUF_W, 1, ctx->stream);
+    ctx->pt.z_c2r(f, f.W, delta_dev, ctx->stream);
+    LAUNCHED(ctx, 3);
+  }
+  const int ns = ctx->nsub[ch];
+  if (P) st = ds_read_bytes(ctx, ch, DS_OFF(P), P, ctx->cfg.n_bins * sizeof(double));
+  if (st == BPS_OK && b) st = ds_read_bytes(ctx, ch, DS_OFF(b), b, ns * sizeof(double));
+  if (st == BPS_OK && nbar) st = ds_read_bytes(ctx, ch, DS_OFF(nbar), nbar, ns * sizeof(double));
+  if (st == BPS_OK && iteration) {
+    unsigned long long it = 0;
+    st = ds_read_bytes(ctx, ch, DS_OFF(iteration), &it, sizeof(it));
+    *iteration = it;
+  }
+  if (st != BPS_OK) return st;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BPS_OK;
+}
+
+// Run n_iter Gibbs iterations of every chain of the groups, recording into
+// `rec_dev` [n_iter][chains][rec_len].  Iterations replay one captured CUDA
+// graph (captured on first use, or again after a change that alters the
+// launches); with kernel timing on they are launched directly instead.
+bps_status run_iterations(bps_ctx* top, const std::vector<bps_ctx*>& groups, int n_iter, double* rec_dev,
+                          int rec_len, int n_chains, bool jump) {
+  bps_ctx* ctx = top;
+  cudaStream_t s = top->stream;
+  for (bps_ctx* g : groups) {
+    launch_reset_rec(g->ds, g->batch, s);
+    LAUNCHED(g, 1);
+  }
+  const long long iter_stride = (long long)n_chains * rec_len;
+  bool use_graph = true;
+  for (bps_ctx* g : groups) use_graph = use_graph && !g->prof;
+  if (!use_graph) {
+    for (int i = 0; i < n_iter; ++i)
+      for (bps_ctx* g : groups) {
+        bps_status st = gibbs_once(g, rec_dev, rec_len, iter_stride, jump);
+        if (st != BPS_OK) return st;
+      }
+    return BPS_OK;
+  }
+  if (top->graph && top->graph_jump != jump) drop_graph(top);
+  if (!top->graph) {
+    // capture on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is replayed on the caller's
+    if (!top->cap_stream) CK(cudaStreamCreateWithFlags(&top->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(s));
+    std::vector<uint64_t> before;
+    for (bps_ctx* gr : groups) before.push_back(gr->launches);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(top->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (bps_ctx* gr : groups) gr->stream = top->cap_stream;
+    bps_status st = BPS_OK;
+    for (bps_ctx* gr : groups) {
+      st = gibbs_once(gr, rec_dev, rec_len, iter_stride, jump);
+      if (st != BPS_OK) break;
+    }
+    for (bps_ctx* gr : groups) gr->stream = s;
+    cudaError_t e = cudaStreamEndCapture(top->cap_stream, &g);
+    // the kernels were captured, not launched: count them per replay instead
+    uint64_t captured = 0;
+    for (size_t i = 0; i < groups.size(); ++i) {
+      captured += groups[i]->launches - before[i];
+      groups[i]->launches = before[i];
+    }
+    if (st != BPS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&top->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    top->graph_jump = jump;
+    top->graph_launches = captured;
+  }
+  for (int i = 0; i < n_iter; ++i) CK(cudaGraphLaunch(top->graph, s));
+  top->launches += (uint64_t)n_iter * top->graph_launches;
+  return BPS_OK;
+}
+
 }  // namespace
 
 void bps::set_last_error(const char* msg) { g_err = msg; }
@@ -419,14 +811,20 @@ void bps::set_last_error(const char* msg) { g_err = msg; }
 // =================================================================== C ABI
 extern "C" {
 
-const char* bps_version(void) { return "bps 0.1 (sm_103a)"; }
+const char* bps_version(void) { return "bps 0.2 (sm_103a)"; }
 
 const char* bps_last_error(const bps_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
-uint64_t bps_kernel_launches(const bps_ctx* ctx) { return ctx ? ctx->launches : 0; }
+uint64_t bps_kernel_launches(const bps_ctx* ctx) {
+  if (!ctx) return 0;
+  uint64_t n = ctx->launches;
+  for (const bps_ctx* g : ctx->groups) n += g->launches;
+  return n;
+}
 
 bps_status bps_profile(bps_ctx* ctx, int enable) {
   if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
+  if (ctx->is_batch) return fail(ctx, BPS_EINVAL, "kernel timing is per single-chain context");
   if (ctx->prof && !enable) prof_fold(ctx);
   ctx->prof = enable != 0;
   return BPS_OK;
@@ -434,6 +832,7 @@ bps_status bps_profile(bps_ctx* ctx, int enable) {
 
 bps_status bps_profile_read(bps_ctx* ctx, double* ms, uint64_t* n) {
   if (!ctx || !ms || !n) return fail(ctx, BPS_EINVAL, "null argument");
+  if (ctx->is_batch) return fail(ctx, BPS_EINVAL, "kernel timing is per single-chain context");
   prof_fold(ctx);
   for (int k = 0; k < 4; ++k) {
     ms[k] = ctx->prof_ms[k];
@@ -448,241 +847,43 @@ bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* c
                       bps_ctx** out) {
   if (!out || !cfg) return fail(nullptr, BPS_EINVAL, "null argument");
   *out = nullptr;
-  PassTable pt;
-  if (!pass_table(grid_n, &pt)) return fail(nullptr, BPS_EINVAL, "unsupported grid size (8,16,32,64,96,128,256)");
-  if (!(box_len > 0.0) || !std::isfinite(box_len)) return fail(nullptr, BPS_EINVAL, "box length must be positive");
   if (n_sub < 1 || n_sub > MAXS) return fail(nullptr, BPS_EINVAL, "n_sub must be in 1..16");
-  if (cfg->n_bins < 1 || cfg->n_bins > MAXB) return fail(nullptr, BPS_EINVAL, "n_bins must be in 1..64");
-  if (cfg->n_leapfrog < 1 || !(cfg->eps_max > 0.0)) return fail(nullptr, BPS_EINVAL, "bad leapfrog settings");
-  if (cfg->jump && (cfg->jump_leapfrog < 1 || !(cfg->jump_eps_max > 0.0)))
-    return fail(nullptr, BPS_EINVAL, "bad jump settings");
-  if (cfg->fixed_bias_index >= n_sub) return fail(nullptr, BPS_EINVAL, "fixed_bias_index out of range");
-  if (cfg->mass_mode != 0 && cfg->mass_mode != 1) return fail(nullptr, BPS_EINVAL, "mass_mode must be 0 or 1");
-
-  DevState h;
-  std::memset(&h, 0, sizeof(h));
-  if (!bin_tables(grid_n, cfg->n_bins, h.thr, h.nmodes))
-    return fail(nullptr, BPS_EINVAL, "a power-spectrum bin holds no mode; use fewer bins");
-  bin_tables(grid_n, cfg->n_bins, h.mthr, nullptr);
-
-  bps_ctx* ctx = new bps_ctx();
-  ctx->N = grid_n;
-  ctx->n_sub = n_sub;
-  ctx->box = box_len;
-  ctx->cfg = *cfg;
-  ctx->stream = (cudaStream_t)cuda_stream;
-  ctx->pt = pt;
-  ctx->zp = pt.zp;
-  ctx->nv = (long long)grid_n * grid_n * grid_n;
-  ctx->Vc = std::pow(box_len / grid_n, 3);
-  ctx->n_spec = (size_t)grid_n * grid_n * pt.zp;
-  ctx->n_mass = cfg->n_bins;
-  ctx->chain_cap = 1024;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  ctx->rebuild_blocks = sms > 0 ? 4 * sms : 512;
-  ctx->n_sm = sms > 0 ? sms : 148;
-  ctx->part_stride = std::max(std::max(pt.x_tiles, pt.z_tiles), ctx->rebuild_blocks);
-
-  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
-  const size_t sb = ctx->n_spec * sizeof(float2), rb = (size_t)ctx->nv * sizeof(float);
-  bool ok = alloc((void**)&ctx->dh[0], sb) && alloc((void**)&ctx->dh[1], sb) && alloc((void**)&ctx->ph, sb) &&
-            alloc((void**)&ctx->W, sb) && alloc((void**)&ctx->a, rb) && alloc((void**)&ctx->c, rb) &&
-            alloc((void**)&ctx->tw, grid_n * sizeof(float2)) &&
-            alloc((void**)&ctx->part, (size_t)region_total() * ctx->part_stride * sizeof(double)) &&
-            alloc((void**)&ctx->ds, sizeof(DevState)) &&
-            alloc((void**)&ctx->chain_dev, (size_t)1024 * (cfg->n_bins + 2 * n_sub + 2) * sizeof(double)) &&
-            cudaMallocHost((void**)&ctx->host_buf, 64 * 1024) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    free_all(ctx);
-    delete ctx;
-    return fail(nullptr, BPS_ENOMEM, "device allocation failed");
-  }
-  // twiddles W_N^j = exp(-2 pi i j / N), FP64 rounded to FP32
-  std::vector<float2> tw(grid_n);
-  for (int j = 0; j < grid_n; ++j) {
-    const double ang = -2.0 * M_PI * (double)j / (double)grid_n;
-    tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-  }
-  for (int m = 0; m < MAXB; ++m) {
-    h.P[m] = 1.0;
-    h.P_ref[m] = 1.0;
-    h.mass_scale[m] = 1.0;
-    h.js[m] = 1.f;
-  }
-  for (int l = 0; l < MAXS; ++l) {
-    h.b[l] = 1.0;
-    h.nbar[l] = 1.0;
-  }
-  cudaStream_t s = ctx->stream;
-  cudaError_t e = cudaMemcpyAsync(ctx->tw, tw.data(), grid_n * sizeof(float2), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ds, &h, sizeof(DevState), cudaMemcpyHostToDevice, s);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(ctx->dh[i], 0, sb, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ph, 0, sb, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->W, 0, sb, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->a, 0, rb, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->c, 0, rb, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    std::string msg = std::string("initialisation failed: ") + cudaGetErrorString(e);
-    free_all(ctx);
-    delete ctx;
-    return fail(nullptr, BPS_ECUDA, msg);
-  }
-  *out = ctx;
-  return BPS_OK;
+  return create_group(grid_n, {box_len}, {n_sub}, {cfg->seed}, {}, cfg, (cudaStream_t)cuda_stream, out);
 }
 
 void bps_destroy(bps_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  for (bps_ctx* g : ctx->groups) bps_destroy(g);
   free_all(ctx);
   delete ctx;
 }
 
-static bps_status set_data_impl(bps_ctx* ctx, const int32_t* counts, const float* R, bool host) {
-  if (!ctx || !counts || !R) return fail(ctx, BPS_EINVAL, "null argument");
-  cudaStream_t s = ctx->stream;
-  const size_t total = (size_t)ctx->n_sub * ctx->nv;
-  if (!ctx->cnt) {
-    if (cudaMalloc((void**)&ctx->cnt, total * sizeof(uint16_t)) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->R, total * sizeof(float)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(ctx->cnt);
-      cudaFree(ctx->R);
-      ctx->cnt = nullptr;
-      ctx->R = nullptr;
-      return fail(ctx, BPS_ENOMEM, "device allocation of the survey data failed");
-    }
-  }
-  const int32_t* cdev = counts;
-  const float* rdev = R;
-  int32_t* ctmp = nullptr;
-  float* rtmp = nullptr;
-  if (host) {
-    // stage through the spectrum work buffers (each at least N^3 * 8 bytes)
-    ctmp = reinterpret_cast<int32_t*>(ctx->ph);
-    rtmp = reinterpret_cast<float*>(ctx->W);
-  }
-  const int blocks = ctx->rebuild_blocks;
-  std::vector<double> hp(4 * (size_t)blocks);
-  std::vector<double> sR(ctx->n_sub), sB(ctx->n_sub), no(ctx->n_sub);
-  double bad = 0.0;
-  for (int l = 0; l < ctx->n_sub; ++l) {
-    const int32_t* cl = cdev + (size_t)l * ctx->nv;
-    const float* rl = rdev + (size_t)l * ctx->nv;
-    if (host) {
-      CK(cudaMemcpyAsync(ctmp, counts + (size_t)l * ctx->nv, ctx->nv * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(rtmp, R + (size_t)l * ctx->nv, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, s));
-      cl = ctmp;
-      rl = rtmp;
-    }
-    launch_data(cl, rl, ctx->cnt + (size_t)l * ctx->nv, ctx->R + (size_t)l * ctx->nv, ctx->nv, ctx->part, blocks,
-                blocks, s);
-    LAUNCHED(ctx, 1);
-    CK(cudaMemcpyAsync(hp.data(), ctx->part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    double v[4] = {0, 0, 0, 0};
-    for (int q = 0; q < 4; ++q)
-      for (int b = 0; b < blocks; ++b) v[q] += hp[(size_t)q * blocks + b];
-    sR[l] = v[0];
-    sB[l] = v[1];
-    no[l] = v[2];
-    bad += v[3];
-  }
-  if (host) {
-    CK(cudaMemsetAsync(ctx->ph, 0, ctx->n_spec * sizeof(float2), s));
-    CK(cudaMemsetAsync(ctx->W, 0, ctx->n_spec * sizeof(float2), s));
-  }
-  if (bad > 0.0) {
-    ctx->have_data = false;
-    return fail(ctx, BPS_EINVAL, "invalid survey data: R < 0 or non-finite, a count outside 0..65535, or a count > 0 where R = 0");
-  }
-  for (int l = 0; l < ctx->n_sub; ++l)
-    if (!(no[l] > 0.0)) return fail(ctx, BPS_EINVAL, "a subsample has no observed voxel (R > 0)");
-  bps_status st = ds_write_bytes(ctx, DS_OFF(sumR), sR.data(), ctx->n_sub * sizeof(double));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, DS_OFF(sumB), sB.data(), ctx->n_sub * sizeof(double));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, DS_OFF(nobs), no.data(), ctx->n_sub * sizeof(double));
-  if (st != BPS_OK) return st;
-  ctx->have_data = true;
-  st = rebuild(ctx);
-  if (st != BPS_OK) return st;
-  CK(cudaStreamSynchronize(s));
-  return BPS_OK;
-}
-
 bps_status bps_set_data(bps_ctx* ctx, const int32_t* counts_dev, const float* R_dev) {
-  return set_data_impl(ctx, counts_dev, R_dev, false);
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
+  return set_data_chain(ctx, 0, counts_dev, R_dev, false);
 }
 
 bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R) {
-  return set_data_impl(ctx, counts, R, true);
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
+  return set_data_chain(ctx, 0, counts, R, true);
 }
 
 bps_status bps_set_state(bps_ctx* ctx, const float* delta_dev, const double* P, const double* b, const double* nbar,
                          uint64_t iteration) {
-  if (!ctx || !P || !b || !nbar) return fail(ctx, BPS_EINVAL, "null argument");
-  const int nb = ctx->cfg.n_bins;
-  for (int m = 0; m < nb; ++m)
-    if (!(P[m] > 0.0) || !std::isfinite(P[m])) return fail(ctx, BPS_EINVAL, "P must be positive and finite");
-  for (int l = 0; l < ctx->n_sub; ++l)
-    if (!std::isfinite(b[l]) || !(nbar[l] > 0.0) || !std::isfinite(nbar[l]))
-      return fail(ctx, BPS_EINVAL, "b must be finite and nbar positive");
-  bps_status st = ds_write_bytes(ctx, DS_OFF(P), P, nb * sizeof(double));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, DS_OFF(P_ref), P, nb * sizeof(double));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, DS_OFF(b), b, ctx->n_sub * sizeof(double));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, DS_OFF(nbar), nbar, ctx->n_sub * sizeof(double));
-  unsigned long long it = iteration;
-  if (st == BPS_OK) st = ds_write_bytes(ctx, DS_OFF(iteration), &it, sizeof(it));
-  if (st != BPS_OK) return st;
-  Fields f = fields(ctx);
-  if (delta_dev) {
-    ctx->pt.z_r2c(f, delta_dev, ctx->W, ctx->stream);
-    ctx->pt.y_fwd(f, BUF_W, ctx->stream);
-    ctx->pt.x_fwd(f, BUF_W, nullptr, ctx->stream);
-    LAUNCHED(ctx, 3);
-    int cur = current_buffer(ctx, &st);
-    if (st != BPS_OK) return st;
-    launch_zero_dc(ctx->dh[cur], ctx->stream);
-    LAUNCHED(ctx, 1);
-  }
-  if (ctx->have_data) {
-    st = rebuild(ctx);
-    if (st != BPS_OK) return st;
-  }
-  CK(cudaStreamSynchronize(ctx->stream));
-  return BPS_OK;
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
+  return set_state_chain(ctx, 0, delta_dev, P, b, nbar, iteration);
 }
 
 bps_status bps_get_state(bps_ctx* ctx, float* delta_dev, double* P, double* b, double* nbar, uint64_t* iteration) {
-  if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
-  bps_status st = BPS_OK;
-  if (delta_dev) {
-    Fields f = fields(ctx);
-    ctx->pt.x_inv(f, -1, ctx->W, ctx->stream);
-    ctx->pt.y_inv(f, BUF_W, ctx->stream);
-    ctx->pt.z_c2r(f, ctx->W, delta_dev, ctx->stream);
-    LAUNCHED(ctx, 3);
-  }
-  if (P) st = ds_read_bytes(ctx, DS_OFF(P), P, ctx->cfg.n_bins * sizeof(double));
-  if (st == BPS_OK && b) st = ds_read_bytes(ctx, DS_OFF(b), b, ctx->n_sub * sizeof(double));
-  if (st == BPS_OK && nbar) st = ds_read_bytes(ctx, DS_OFF(nbar), nbar, ctx->n_sub * sizeof(double));
-  if (st == BPS_OK && iteration) {
-    unsigned long long it = 0;
-    st = ds_read_bytes(ctx, DS_OFF(iteration), &it, sizeof(it));
-    *iteration = it;
-  }
-  if (st != BPS_OK) return st;
-  CK(cudaStreamSynchronize(ctx->stream));
-  return BPS_OK;
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
+  return get_state_chain(ctx, 0, delta_dev, P, b, nbar, iteration);
 }
 
 bps_status bps_get_spectrum(bps_ctx* ctx, float* spec_dev) {
-  if (!ctx || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument");
+  if (!ctx || ctx->is_batch || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument or batch context");
   bps_status st;
-  int cur = current_buffer(ctx, &st);
+  int cur = current_buffer(ctx, 0, &st);
   if (st != BPS_OK) return st;
   st = copy_spec_out(ctx, ctx->dh[cur], spec_dev);
   if (st != BPS_OK) return st;
@@ -691,9 +892,9 @@ bps_status bps_get_spectrum(bps_ctx* ctx, float* spec_dev) {
 }
 
 bps_status bps_set_spectrum(bps_ctx* ctx, const float* spec_dev) {
-  if (!ctx || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument");
+  if (!ctx || ctx->is_batch || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument or batch context");
   bps_status st;
-  int cur = current_buffer(ctx, &st);
+  int cur = current_buffer(ctx, 0, &st);
   if (st != BPS_OK) return st;
   st = copy_spec_in(ctx, spec_dev, ctx->dh[cur]);
   if (st != BPS_OK) return st;
@@ -711,9 +912,9 @@ bps_status bps_hmc_step(bps_ctx* ctx, bps_move_info* info) {
   if (info) {
     int acc = 0;
     double dH = 0, eps = 0;
-    st = ds_read_bytes(ctx, DS_OFF(accepted), &acc, sizeof(int));
-    if (st == BPS_OK) st = ds_read_bytes(ctx, DS_OFF(dH), &dH, sizeof(double));
-    if (st == BPS_OK) st = ds_read_bytes(ctx, DS_OFF(eps), &eps, sizeof(double));
+    st = ds_read_bytes(ctx, 0, DS_OFF(accepted), &acc, sizeof(int));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(dH), &dH, sizeof(double));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(eps), &eps, sizeof(double));
     if (st != BPS_OK) return st;
     info->accepted = acc;
     info->dH = dH;
@@ -728,8 +929,8 @@ bps_status bps_sample_power(bps_ctx* ctx, double* P_out, double* sigma_out) {
   if (st != BPS_OK) return st;
   st = power_stage(ctx, true, true);
   if (st != BPS_OK) return st;
-  if (P_out) st = ds_read_bytes(ctx, DS_OFF(P), P_out, ctx->cfg.n_bins * sizeof(double));
-  if (st == BPS_OK && sigma_out) st = ds_read_bytes(ctx, DS_OFF(sigma), sigma_out, ctx->cfg.n_bins * sizeof(double));
+  if (P_out) st = ds_read_bytes(ctx, 0, DS_OFF(P), P_out, ctx->cfg.n_bins * sizeof(double));
+  if (st == BPS_OK && sigma_out) st = ds_read_bytes(ctx, 0, DS_OFF(sigma), sigma_out, ctx->cfg.n_bins * sizeof(double));
   if (st != BPS_OK) return st;
   if (P_out || sigma_out) return check_status(ctx);
   return BPS_OK;
@@ -740,12 +941,13 @@ bps_status bps_sample_bias_norm(bps_ctx* ctx, double* b_out, double* nbar_out, d
   if (st != BPS_OK) return st;
   st = bias_stage(ctx, true);
   if (st != BPS_OK) return st;
-  if (b_out) st = ds_read_bytes(ctx, DS_OFF(b), b_out, ctx->n_sub * sizeof(double));
-  if (st == BPS_OK && nbar_out) st = ds_read_bytes(ctx, DS_OFF(nbar), nbar_out, ctx->n_sub * sizeof(double));
+  const int ns = ctx->nsub[0];
+  if (b_out) st = ds_read_bytes(ctx, 0, DS_OFF(b), b_out, ns * sizeof(double));
+  if (st == BPS_OK && nbar_out) st = ds_read_bytes(ctx, 0, DS_OFF(nbar), nbar_out, ns * sizeof(double));
   if (st == BPS_OK && sums_out) {
     std::vector<double> tmp(3 * MAXS);
-    st = ds_read_bytes(ctx, DS_OFF(sums), tmp.data(), tmp.size() * sizeof(double));
-    for (int i = 0; i < 3 * ctx->n_sub; ++i) sums_out[i] = tmp[i];
+    st = ds_read_bytes(ctx, 0, DS_OFF(sums), tmp.data(), tmp.size() * sizeof(double));
+    for (int i = 0; i < 3 * ns; ++i) sums_out[i] = tmp[i];
   }
   if (st != BPS_OK) return st;
   if (b_out || nbar_out || sums_out) return check_status(ctx);
@@ -762,9 +964,9 @@ bps_status bps_jump(bps_ctx* ctx, bps_move_info* info) {
   if (info) {
     int acc = 0;
     double dH = 0, eps = 0;
-    st = ds_read_bytes(ctx, DS_OFF(jaccepted), &acc, sizeof(int));
-    if (st == BPS_OK) st = ds_read_bytes(ctx, DS_OFF(jdH), &dH, sizeof(double));
-    if (st == BPS_OK) st = ds_read_bytes(ctx, DS_OFF(jeps), &eps, sizeof(double));
+    st = ds_read_bytes(ctx, 0, DS_OFF(jaccepted), &acc, sizeof(int));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(jdH), &dH, sizeof(double));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(jeps), &eps, sizeof(double));
     if (st != BPS_OK) return st;
     info->accepted = acc;
     info->dH = dH;
@@ -778,34 +980,18 @@ bps_status bps_gibbs_iterate(bps_ctx* ctx, int n_iter, double* chain_out) {
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   if (n_iter < 0) return fail(ctx, BPS_EINVAL, "n_iter must be >= 0");
-  const int rec = ctx->cfg.n_bins + 2 * ctx->n_sub + 2;
-  if (chain_out && n_iter > ctx->chain_cap) {
-    cudaFree(ctx->chain_dev);
-    ctx->chain_dev = nullptr;
-    ctx->chain_cap = 0;
-    if (cudaMalloc((void**)&ctx->chain_dev, (size_t)n_iter * rec * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, BPS_ENOMEM, "chain buffer allocation failed");
-    }
-    ctx->chain_cap = n_iter;
-  }
-  ScalarArgs sa = scalars(ctx);
-  for (int i = 0; i < n_iter; ++i) {
-    st = hmc_move(ctx, false);
-    if (st == BPS_OK) st = power_stage(ctx, true, false);
-    if (st == BPS_OK && ctx->cfg.jump) st = jump_stage(ctx, false);
-    if (st == BPS_OK) st = bias_stage(ctx, false);
+  if (n_iter == 0) return BPS_OK;
+  const int rec = ctx->cfg.n_bins + 2 * ctx->max_sub + 2;
+  // the record buffer holds up to chain_cap iterations; longer runs go in pieces
+  int done = 0;
+  while (done < n_iter) {
+    const int k = std::min(n_iter - done, ctx->chain_cap);
+    st = run_iterations(ctx, {ctx}, k, ctx->chain_dev, rec, 1, ctx->cfg.jump != 0);
     if (st != BPS_OK) return st;
-    if (chain_out) {
-      launch_record(sa, ctx->chain_dev + (size_t)i * rec, ctx->stream);
-      LAUNCHED(ctx, 1);
-    }
-    launch_advance(ctx->ds, ctx->stream);
-    LAUNCHED(ctx, 1);
-  }
-  if (chain_out && n_iter > 0) {
-    CK(cudaMemcpyAsync(chain_out, ctx->chain_dev, (size_t)n_iter * rec * sizeof(double), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    if (chain_out)
+      CK(cudaMemcpyAsync(chain_out + (size_t)done * rec, ctx->chain_dev, (size_t)k * rec * sizeof(double),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    done += k;
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return check_status(ctx);
@@ -816,22 +1002,28 @@ bps_status bps_set_mass_scale(bps_ctx* ctx, int n_mass_bins, const double* scale
   if (n_mass_bins < 1 || n_mass_bins > MAXB) return fail(ctx, BPS_EINVAL, "n_mass_bins must be in 1..64");
   for (int j = 0; j < n_mass_bins; ++j)
     if (!(scales[j] > 0.0) || !std::isfinite(scales[j])) return fail(ctx, BPS_EINVAL, "scales must be positive");
-  int thr[MAXB];
-  if (!bin_tables(ctx->N, n_mass_bins, thr, nullptr))
-    return fail(ctx, BPS_EINVAL, "a mass bin holds no |n|^2 value; use fewer mass bins");
-  bps_status st = ds_write_bytes(ctx, DS_OFF(mthr), thr, sizeof(thr));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, DS_OFF(mass_scale), scales, n_mass_bins * sizeof(double));
-  if (st != BPS_OK) return st;
-  ctx->n_mass = n_mass_bins;
+  std::vector<bps_ctx*> gs = ctx->is_batch ? ctx->groups : std::vector<bps_ctx*>{ctx};
+  for (bps_ctx* g : gs) {
+    int thr[MAXB];
+    if (!bin_tables(g->N, n_mass_bins, thr, nullptr))
+      return fail(ctx, BPS_EINVAL, "a mass bin holds no |n|^2 value; use fewer mass bins");
+    for (int ch = 0; ch < g->batch; ++ch) {
+      bps_status st = ds_write_bytes(g, ch, DS_OFF(mthr), thr, sizeof(thr));
+      if (st == BPS_OK) st = ds_write_bytes(g, ch, DS_OFF(mass_scale), scales, n_mass_bins * sizeof(double));
+      if (st != BPS_OK) return st;
+    }
+    g->n_mass = n_mass_bins;
+  }
+  drop_graph(ctx);   // the number of mass bins is a launch argument
   return BPS_OK;
 }
 
 bps_status bps_fft_r2c(bps_ctx* ctx, const float* real_dev, float* spec_dev) {
-  if (!ctx || !real_dev || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument");
-  Fields f = fields(ctx);
+  if (!ctx || ctx->is_batch || !real_dev || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument or batch context");
+  Fields f = fields_at(ctx, 0);
   ctx->pt.z_r2c(f, real_dev, ctx->W, ctx->stream);
-  ctx->pt.y_fwd(f, BUF_W, ctx->stream);
-  ctx->pt.x_fwd(f, BUF_W, ctx->W, ctx->stream);
+  ctx->pt.y_fwd(f, BUF_W, 1, ctx->stream);
+  ctx->pt.x_fwd(f, BUF_W, ctx->W, 1, ctx->stream);
   LAUNCHED(ctx, 3);
   bps_status st = copy_spec_out(ctx, ctx->W, spec_dev);
   if (st != BPS_OK) return st;
@@ -840,12 +1032,12 @@ bps_status bps_fft_r2c(bps_ctx* ctx, const float* real_dev, float* spec_dev) {
 }
 
 bps_status bps_fft_c2r(bps_ctx* ctx, const float* spec_dev, float* real_dev) {
-  if (!ctx || !real_dev || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument");
+  if (!ctx || ctx->is_batch || !real_dev || !spec_dev) return fail(ctx, BPS_EINVAL, "null argument or batch context");
   bps_status st = copy_spec_in(ctx, spec_dev, ctx->W);
   if (st != BPS_OK) return st;
-  Fields f = fields(ctx);
-  ctx->pt.x_inv(f, BUF_W, ctx->W, ctx->stream);
-  ctx->pt.y_inv(f, BUF_W, ctx->stream);
+  Fields f = fields_at(ctx, 0);
+  ctx->pt.x_inv(f, BUF_W, ctx->W, 1, ctx->stream);
+  ctx->pt.y_inv(f, BUF_W, 1, ctx->stream);
   ctx->pt.z_c2r(f, ctx->W, real_dev, ctx->stream);
   LAUNCHED(ctx, 3);
   CK(cudaStreamSynchronize(ctx->stream));
@@ -856,27 +1048,143 @@ bps_status bps_gradient(bps_ctx* ctx, float* grad_dev, double* energies) {
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   if (!grad_dev) return fail(ctx, BPS_EINVAL, "null argument");
-  Fields f = fields(ctx);
-  ScalarArgs sa = scalars(ctx);
+  Fields f = fields_at(ctx, 0);
+  ScalarArgs sa = scalars_at(ctx, 0);
   cudaStream_t s = ctx->stream;
-  launch_move_begin(sa, s);   // per-bin tables of the current P and abar
-  ctx->pt.x_inv(f, -1, ctx->W, s);
-  ctx->pt.y_inv(f, BUF_W, s);
-  ctx->pt.z_grad(f, region_offset(ctx, RG_LIK0), s);
-  ctx->pt.y_fwd(f, BUF_W, s);
-  ctx->pt.x_grad(f, ctx->W, region_offset(ctx, RG_GRAD), s);
-  launch_reduce_to(sa, region_offset(ctx, RG_GRAD), ctx->pt.x_tiles, 1, 0.5 / (double)ctx->nv,
-                   reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->ds) + DS_OFF(scratch)), s);
-  launch_reduce_to(sa, region_offset(ctx, RG_LIK0), ctx->pt.z_tiles, 1, 1.0,
-                   reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->ds) + DS_OFF(scratch)) + 1, s);
+  launch_move_begin(sa, 1, s);   // per-bin tables of the current P and abar
+  ctx->pt.x_inv(f, -1, ctx->W, 1, s);
+  ctx->pt.y_inv(f, BUF_W, 1, s);
+  ctx->pt.z_grad(f, region_offset(ctx, RG_LIK0), 1, s);
+  ctx->pt.y_fwd(f, BUF_W, 1, s);
+  ctx->pt.x_grad(f, ctx->W, region_offset(ctx, RG_GRAD), 1, s);
+  double* scratch = reinterpret_cast<double*>(ds_addr(ctx, 0, DS_OFF(scratch)));
+  launch_reduce_to(sa, region_offset(ctx, RG_GRAD), ctx->pt.x_tiles, 1, 0.5 / (double)ctx->nv, scratch, s);
+  launch_reduce_to(sa, region_offset(ctx, RG_LIK0), ctx->pt.z_tiles, 1, 1.0, scratch + 1, s);
   LAUNCHED(ctx, 8);
   st = copy_spec_out(ctx, ctx->W, grad_dev);
   if (st != BPS_OK) return st;
   if (energies) {
-    st = ds_read_bytes(ctx, DS_OFF(scratch), energies, 2 * sizeof(double));
+    st = ds_read_bytes(ctx, 0, DS_OFF(scratch), energies, 2 * sizeof(double));
     if (st != BPS_OK) return st;
   }
   CK(cudaStreamSynchronize(s));
+  return BPS_OK;
+}
+
+// ------------------------------------------------------------------ batches
+bps_status bps_create_batch(int n_chains, const int* grid_n, const double* box_len, const int* n_sub,
+                            const bps_config* cfg, void* cuda_stream, bps_ctx** out) {
+  if (!out || !cfg || !grid_n || !box_len || !n_sub) return fail(nullptr, BPS_EINVAL, "null argument");
+  *out = nullptr;
+  if (n_chains < 1) return fail(nullptr, BPS_EINVAL, "n_chains must be >= 1");
+  std::map<int, std::vector<int>> by_n;
+  int max_sub = 0;
+  for (int j = 0; j < n_chains; ++j) {
+    by_n[grid_n[j]].push_back(j);
+    if (n_sub[j] < 1 || n_sub[j] > MAXS) return fail(nullptr, BPS_EINVAL, "n_sub must be in 1..16");
+    max_sub = std::max(max_sub, n_sub[j]);
+  }
+  bps_ctx* top = new bps_ctx();
+  top->is_batch = true;
+  top->cfg = *cfg;
+  top->stream = (cudaStream_t)cuda_stream;
+  top->max_sub = max_sub;
+  top->rec_len_all = cfg->n_bins + 2 * max_sub + 2;
+  top->chain_map.assign(n_chains, {-1, -1});
+  top->batch = 0;
+  int slot = 0;
+  for (auto& kv : by_n) {
+    std::vector<double> box;
+    std::vector<int> ns, ids;
+    std::vector<uint64_t> seeds;
+    for (size_t i = 0; i < kv.second.size(); ++i) {
+      const int j = kv.second[i];
+      box.push_back(box_len[j]);
+      ns.push_back(n_sub[j]);
+      seeds.push_back(cfg->seed + (uint64_t)j);
+      ids.push_back(slot + (int)i);   // the records of one group occupy consecutive slots
+    }
+    bps_ctx* g = nullptr;
+    bps_status st = create_group(kv.first, box, ns, seeds, ids, cfg, top->stream, &g);
+    if (st != BPS_OK) {
+      bps_destroy(top);
+      return st;
+    }
+    const int gi = (int)top->groups.size();
+    top->groups.push_back(g);
+    for (size_t i = 0; i < kv.second.size(); ++i) top->chain_map[kv.second[i]] = {gi, (int)i};
+    slot += (int)kv.second.size();
+  }
+  top->chain_cap = 256;
+  if (cudaMalloc((void**)&top->chain_dev, (size_t)top->chain_cap * n_chains * top->rec_len_all * sizeof(double)) !=
+          cudaSuccess ||
+      cudaMallocHost((void**)&top->host_buf, 64 * 1024) != cudaSuccess) {
+    cudaGetLastError();
+    bps_destroy(top);
+    return fail(nullptr, BPS_ENOMEM, "device allocation failed");
+  }
+  *out = top;
+  return BPS_OK;
+}
+
+int bps_batch_record_len(const bps_ctx* batch) { return batch && batch->is_batch ? batch->rec_len_all : 0; }
+
+int bps_batch_record_slot(const bps_ctx* batch, int chain) {
+  if (!batch || !batch->is_batch || chain < 0 || chain >= (int)batch->chain_map.size()) return -1;
+  const auto& cm = batch->chain_map[chain];
+  return batch->groups[cm.first]->chain_id[cm.second];
+}
+
+bps_status bps_batch_set_chain(bps_ctx* batch, int chain, const int32_t* counts_dev, const float* R_dev,
+                               const float* delta_dev, const double* P, const double* b, const double* nbar,
+                               uint64_t iteration) {
+  if (!batch || !batch->is_batch) return fail(batch, BPS_EINVAL, "not a batch context");
+  if (chain < 0 || chain >= (int)batch->chain_map.size()) return fail(batch, BPS_EINVAL, "chain out of range");
+  bps_ctx* g = batch->groups[batch->chain_map[chain].first];
+  const int ch = batch->chain_map[chain].second;
+  bps_status st = set_data_chain(g, ch, counts_dev, R_dev, false);
+  if (st == BPS_OK) st = set_state_chain(g, ch, delta_dev, P, b, nbar, iteration);
+  if (st != BPS_OK) batch->err = g->err;
+  return st;
+}
+
+bps_status bps_batch_get_chain(bps_ctx* batch, int chain, float* delta_dev, double* P, double* b, double* nbar,
+                               uint64_t* iteration) {
+  if (!batch || !batch->is_batch) return fail(batch, BPS_EINVAL, "not a batch context");
+  if (chain < 0 || chain >= (int)batch->chain_map.size()) return fail(batch, BPS_EINVAL, "chain out of range");
+  bps_ctx* g = batch->groups[batch->chain_map[chain].first];
+  bps_status st = get_state_chain(g, batch->chain_map[chain].second, delta_dev, P, b, nbar, iteration);
+  if (st != BPS_OK) batch->err = g->err;
+  return st;
+}
+
+bps_status bps_batch_gibbs_iterate(bps_ctx* batch, int n_iter, double* chain_out) {
+  if (!batch || !batch->is_batch) return fail(batch, BPS_EINVAL, "not a batch context");
+  if (n_iter < 0) return fail(batch, BPS_EINVAL, "n_iter must be >= 0");
+  for (bps_ctx* g : batch->groups)
+    for (int ch = 0; ch < g->batch; ++ch)
+      if (!g->have_data[ch]) return fail(batch, BPS_ESTATE, "a chain has no data (bps_batch_set_chain)");
+  bps_ctx* ctx = batch;
+  const int n_chains = (int)batch->chain_map.size();
+  const int rec = batch->rec_len_all;
+  int done = 0;
+  while (done < n_iter) {
+    const int k = std::min(n_iter - done, batch->chain_cap);
+    bps_status st = run_iterations(batch, batch->groups, k, batch->chain_dev, rec, n_chains, batch->cfg.jump != 0);
+    if (st != BPS_OK) return st;
+    if (chain_out)
+      CK(cudaMemcpyAsync(chain_out + (size_t)done * n_chains * rec, batch->chain_dev,
+                         (size_t)k * n_chains * rec * sizeof(double), cudaMemcpyDeviceToHost, batch->stream));
+    done += k;
+  }
+  CK(cudaStreamSynchronize(batch->stream));
+  for (bps_ctx* g : batch->groups) {
+    bps_status st = check_status(g);
+    if (st != BPS_OK) {
+      batch->err = g->err;
+      return st;
+    }
+  }
   return BPS_OK;
 }
 

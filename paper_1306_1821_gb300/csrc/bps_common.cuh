@@ -264,6 +264,11 @@ struct DevState {
   int thr[MAXB];                     // smallest |n|^2 of each P bin
   int mthr[MAXB];                    // smallest |n|^2 of each mass-scale bin
   double scratch[8];                 // small results handed to the host
+  // per-chain constants (chains of one batch share the kernels, not these)
+  double vc;                         // cell volume V_cell
+  unsigned long long seed;           // Philox key
+  int nsub;                          // galaxy subsamples of this chain
+  int rec_idx;                       // next slot of the chain record buffer
   unsigned long long iteration;
   unsigned long long n_moves, n_accepted;
 };

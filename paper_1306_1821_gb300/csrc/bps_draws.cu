@@ -14,6 +14,13 @@ namespace bps {
 
 constexpr int MAX_ATTEMPTS = 64;
 
+// the scalar arguments of chain `ch` of a batch (blockIdx.y)
+__device__ __forceinline__ ScalarArgs chain_args(ScalarArgs a, int ch) {
+  a.ds += ch;
+  a.part += ch * a.cstride;
+  return a;
+}
+
 // Deterministic sum of n partials (stride 1) by one block of 256 threads;
 // the value is valid in thread 0.
 __device__ double sum_partials(const double* p, int n, double* sh) {
@@ -23,18 +30,19 @@ __device__ double sum_partials(const double* p, int n, double* sh) {
 }
 
 // ------------------------------------------------------------------ HMC move
-__global__ void k_move_begin(ScalarArgs a) {
+__global__ void k_move_begin(ScalarArgs a0) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   DevState* ds = a.ds;
   const int t = threadIdx.x;
   if (t == 0) {
-    P4 r = philox(0, ds->iteration, ST_HMC, 0, a.seed);
+    P4 r = philox(0, ds->iteration, ST_HMC, 0, ds->seed);
     ds->eps = a.eps_max * u52(r.w[0]);
     ds->u_acc = u52(r.w[1]);
   }
   if (t < MAXB) {
     if (t < a.n_bins) {
       // lambda_m = P_m / V_cell (Eq. dens_prior in Fourier space); M = 1/lambda + abar (Eq. Mass_matrix)
-      const double il = a.Vc / ds->P[t];
+      const double il = ds->vc / ds->P[t];
       const double M = il + ds->abar;
       ds->inv_lambda[t] = (float)il;
       ds->inv_M[t] = (float)(1.0 / M);
@@ -51,7 +59,8 @@ __global__ void k_move_begin(ScalarArgs a) {
 }
 
 // H = (1/2N^3) sum w (|p|^2/M + |delta|^2/lambda) + (1/2) sum (a delta^2 - 2 c delta)
-__global__ void k_move_end(ScalarArgs a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz) {
+__global__ void k_move_end(ScalarArgs a0, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
   DevState* ds = a.ds;
   const double h = 0.5 * a.inv_nv;
@@ -117,18 +126,19 @@ __device__ double gamma_mt(double shape, uint64_t seed, uint64_t it, int m, int*
 
 // block m: sigma_m = (V_cell/N^3) sum_{k in m} w |delta_k|^2; then (draw) P_m = sigma_m / x,
 // x ~ chi^2_beta = 2 Gamma(beta/2), beta = n_m + 2 alpha - 2 (Sec. 4.2, Eq. XI_SQUARE)
-__global__ void k_power(ScalarArgs a, int region, int nx, int draw) {
+__global__ void k_power(ScalarArgs a0, int region, int nx, int draw) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
   DevState* ds = a.ds;
   const int m = blockIdx.x;
   const double s = sum_partials(a.part + region + (size_t)m * a.stride, nx, sh);
   if (threadIdx.x == 0) {
-    const double sigma = s * a.Vc * a.inv_nv;
+    const double sigma = s * ds->vc * a.inv_nv;
     ds->sigma[m] = sigma;
     if (draw) {
       const double beta = ds->nmodes[m] + 2.0 * a.alpha - 2.0;
       int fail = 0;
-      const double g = gamma_mt(0.5 * beta, a.seed, ds->iteration, m, &fail);
+      const double g = gamma_mt(0.5 * beta, ds->seed, ds->iteration, m, &fail);
       if (fail || !(sigma > 0.0)) atomicOr(&ds->status, ST_DRAW_FAIL);
       else ds->P[m] = sigma / (2.0 * g);
     }
@@ -200,10 +210,12 @@ __device__ double gig_draw(double p, double A, double B, uint64_t seed, uint64_t
 // block l: S1 = sum N delta, S2 = sum R delta, S3 = sum R delta^2; then
 // b_l ~ N(D/C, 1/C), C = Nbar S3, D = S1 - Nbar S2 (Sec. 3.5, App. B; skipped for
 // the fixed index) and Nbar_l ~ GIG(1 - N_obs/2, sum R + 2 b S2 + b^2 S3, sum N^2/R)
-__global__ void k_bias_nbar(ScalarArgs a, int region, int nz) {
+__global__ void k_bias_nbar(ScalarArgs a0, int region, int nz) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
   DevState* ds = a.ds;
   const int l = blockIdx.x;
+  if (l >= ds->nsub) return;
   double S[3];
   for (int q = 0; q < 3; ++q) S[q] = sum_partials(a.part + region + (size_t)(3 * l + q) * a.stride, nz, sh);
   if (threadIdx.x == 0) {
@@ -217,7 +229,7 @@ __global__ void k_bias_nbar(ScalarArgs a, int region, int nz) {
     if (l != a.fixed_bias) {
       const double C = nb * S[2];
       const double D = S[0] - nb * S[1];
-      P4 r = philox((uint64_t)l, it, ST_BIAS, 0, a.seed);
+      P4 r = philox((uint64_t)l, it, ST_BIAS, 0, ds->seed);
       const double z = normal64(r.w[0], r.w[1]);
       if (C > 0.0) b = D / C + z / sqrt(C);
       else fail = 1;
@@ -225,7 +237,7 @@ __global__ void k_bias_nbar(ScalarArgs a, int region, int nz) {
     const double A = ds->sumR[l] + 2.0 * b * S[1] + b * b * S[2];
     const double p = 1.0 - 0.5 * ds->nobs[l];
     double x = nb;
-    if (A > 0.0 && ds->sumB[l] > 0.0) x = gig_draw(p, A, ds->sumB[l], a.seed, it, l, &fail);
+    if (A > 0.0 && ds->sumB[l] > 0.0) x = gig_draw(p, A, ds->sumB[l], ds->seed, it, l, &fail);
     else fail = 1;
     if (fail || !isfinite(b) || !isfinite(x)) {
       atomicOr(&ds->status, ST_DRAW_FAIL);
@@ -236,7 +248,8 @@ __global__ void k_bias_nbar(ScalarArgs a, int region, int nz) {
   }
 }
 
-__global__ void k_abar(ScalarArgs a, int region, int nblk) {
+__global__ void k_abar(ScalarArgs a0, int region, int nblk) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
   const double s = sum_partials(a.part + region, nblk, sh);
   if (threadIdx.x == 0) a.ds->abar = s * a.inv_nv;
@@ -246,20 +259,21 @@ __global__ void k_abar(ScalarArgs a, int region, int nblk) {
 // HMC in theta = ln P with the whitened field fixed (Sec. 4.3, App. C).
 // Mass mu_m = max(1, abar P_ref_m sigma_m / (4 V_cell P_m)): built from the
 // whitened field and a fixed reference spectrum, never from the current P.
-__global__ void k_jump_begin(ScalarArgs a) {
+__global__ void k_jump_begin(ScalarArgs a0) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   DevState* ds = a.ds;
   const int m = threadIdx.x;
   const uint64_t it = ds->iteration;
   if (m == 0) {
-    P4 r = philox(0, it, ST_JUMP, 0, a.seed);
+    P4 r = philox(0, it, ST_JUMP, 0, ds->seed);
     ds->jeps = a.jeps_max * u52(r.w[0]);
     ds->ju_acc = u52(r.w[1]);
     ds->jaccepted = 0;
   }
   if (m < MAXB) {
     if (m < a.n_bins) {
-      const double mu = fmax(1.0, ds->abar * ds->P_ref[m] * ds->sigma[m] / (4.0 * a.Vc * ds->P[m]));
-      P4 r = philox((uint64_t)m, it, ST_JUMP_MOM, 0, a.seed);
+      const double mu = fmax(1.0, ds->abar * ds->P_ref[m] * ds->sigma[m] / (4.0 * ds->vc * ds->P[m]));
+      P4 r = philox((uint64_t)m, it, ST_JUMP_MOM, 0, ds->seed);
       ds->mu[m] = mu;
       ds->rho[m] = sqrt(mu) * normal64(r.w[0], r.w[1]);
       ds->th[m] = log(ds->P[m]);
@@ -270,7 +284,8 @@ __global__ void k_jump_begin(ScalarArgs a) {
 
 // blocks m < n_bins: gradient d psi_J / d theta_m = (alpha - 1) + (1/2N^3) sum_{k in m} w Re(conj(g) delta);
 // block n_bins: likelihood energy at theta
-__global__ void k_jump_reduce(ScalarArgs a, int r_grad, int nx, int r_lik, int nz) {
+__global__ void k_jump_reduce(ScalarArgs a0, int r_grad, int nx, int r_lik, int nz) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
   DevState* ds = a.ds;
   const int m = blockIdx.x;
@@ -283,7 +298,8 @@ __global__ void k_jump_reduce(ScalarArgs a, int r_grad, int nx, int r_lik, int n
   }
 }
 
-__global__ void k_jump_update(ScalarArgs a, int kind) {
+__global__ void k_jump_update(ScalarArgs a0, int kind) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
   DevState* ds = a.ds;
   const int m = threadIdx.x;   // 64 threads
@@ -344,48 +360,64 @@ __global__ void k_reduce_to(ScalarArgs a, int region, int nblk, double scale, do
   if (threadIdx.x == 0) out[q] = s * scale;
 }
 
-// chain record: P[n_bins], b[n_sub], nbar[n_sub], dH, accepted
-__global__ void k_record(ScalarArgs a, double* rec) {
+// chain record: P[n_bins], b[n_sub], nbar[n_sub], dH, accepted; slot rec_idx
+// of chain (chain0 + blockIdx.y) in a buffer laid out [slot][chain][rec_len]
+__global__ void k_record(ScalarArgs a0, double* rec0, int rec_len, long long iter_stride, int chain0) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
   DevState* ds = a.ds;
   const int t = threadIdx.x;
+  const int ns = ds->nsub;
+  double* rec = rec0 + (long long)ds->rec_idx * iter_stride + (long long)(chain0 + blockIdx.y) * rec_len;
   if (t < a.n_bins) rec[t] = ds->P[t];
-  if (t < a.n_sub) {
+  if (t < ns) {
     rec[a.n_bins + t] = ds->b[t];
-    rec[a.n_bins + a.n_sub + t] = ds->nbar[t];
+    rec[a.n_bins + ns + t] = ds->nbar[t];
   }
   if (t == 0) {
-    rec[a.n_bins + 2 * a.n_sub] = ds->dH;
-    rec[a.n_bins + 2 * a.n_sub + 1] = (double)ds->accepted;
+    rec[a.n_bins + 2 * ns] = ds->dH;
+    rec[a.n_bins + 2 * ns + 1] = (double)ds->accepted;
   }
+  __syncthreads();
+  if (t == 0) ds->rec_idx += 1;
 }
 
-__global__ void k_advance(DevState* ds) { ds->iteration += 1; }
+__global__ void k_advance(DevState* ds) { ds[blockIdx.x].iteration += 1; }
+
+__global__ void k_reset_rec(DevState* ds) { ds[blockIdx.x].rec_idx = 0; }
 
 __global__ void k_zero_dc(float2* spec) { spec[0] = make_float2(0.f, 0.f); }
 
-void launch_move_begin(const ScalarArgs& a, cudaStream_t s) { k_move_begin<<<1, MAXB, 0, s>>>(a); }
-void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz,
+void launch_move_begin(const ScalarArgs& a, int nch, cudaStream_t s) { k_move_begin<<<dim3(1, nch), MAXB, 0, s>>>(a); }
+void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz, int nch,
                      cudaStream_t s) {
-  k_move_end<<<1, 256, 0, s>>>(a, r_init, r_lik0, r_final, r_lik1, nx, nz);
+  k_move_end<<<dim3(1, nch), 256, 0, s>>>(a, r_init, r_lik0, r_final, r_lik1, nx, nz);
 }
-void launch_power(const ScalarArgs& a, int region, int nx, int draw, cudaStream_t s) {
-  k_power<<<a.n_bins, 256, 0, s>>>(a, region, nx, draw);
+void launch_power(const ScalarArgs& a, int region, int nx, int draw, int nch, cudaStream_t s) {
+  k_power<<<dim3(a.n_bins, nch), 256, 0, s>>>(a, region, nx, draw);
 }
-void launch_bias_nbar(const ScalarArgs& a, int region, int nz, cudaStream_t s) {
-  k_bias_nbar<<<a.n_sub, 256, 0, s>>>(a, region, nz);
+void launch_bias_nbar(const ScalarArgs& a, int region, int nz, int nch, cudaStream_t s) {
+  k_bias_nbar<<<dim3(a.max_sub, nch), 256, 0, s>>>(a, region, nz);
 }
-void launch_abar(const ScalarArgs& a, int region, int nblk, cudaStream_t s) { k_abar<<<1, 256, 0, s>>>(a, region, nblk); }
-void launch_jump_begin(const ScalarArgs& a, cudaStream_t s) { k_jump_begin<<<1, MAXB, 0, s>>>(a); }
-void launch_jump_reduce(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, cudaStream_t s) {
-  k_jump_reduce<<<a.n_bins + 1, 256, 0, s>>>(a, r_grad, nx, r_lik, nz);
+void launch_abar(const ScalarArgs& a, int region, int nblk, int nch, cudaStream_t s) {
+  k_abar<<<dim3(1, nch), 256, 0, s>>>(a, region, nblk);
 }
-void launch_jump_update(const ScalarArgs& a, int kind, cudaStream_t s) { k_jump_update<<<1, MAXB, 0, s>>>(a, kind); }
+void launch_jump_begin(const ScalarArgs& a, int nch, cudaStream_t s) { k_jump_begin<<<dim3(1, nch), MAXB, 0, s>>>(a); }
+void launch_jump_reduce(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, int nch, cudaStream_t s) {
+  k_jump_reduce<<<dim3(a.n_bins + 1, nch), 256, 0, s>>>(a, r_grad, nx, r_lik, nz);
+}
+void launch_jump_update(const ScalarArgs& a, int kind, int nch, cudaStream_t s) {
+  k_jump_update<<<dim3(1, nch), MAXB, 0, s>>>(a, kind);
+}
 void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, double scale, double* out_dev,
                       cudaStream_t s) {
   k_reduce_to<<<count, 256, 0, s>>>(a, region, nblk, scale, out_dev);
 }
-void launch_record(const ScalarArgs& a, double* rec_dev, cudaStream_t s) { k_record<<<1, MAXB, 0, s>>>(a, rec_dev); }
-void launch_advance(DevState* ds, cudaStream_t s) { k_advance<<<1, 1, 0, s>>>(ds); }
+void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long iter_stride, int chain0, int nch,
+                   cudaStream_t s) {
+  k_record<<<dim3(1, nch), MAXB, 0, s>>>(a, rec_dev, rec_len, iter_stride, chain0);
+}
+void launch_advance(DevState* ds, int nch, cudaStream_t s) { k_advance<<<nch, 1, 0, s>>>(ds); }
+void launch_reset_rec(DevState* ds, int nch, cudaStream_t s) { k_reset_rec<<<nch, 1, 0, s>>>(ds); }
 void launch_zero_dc(float2* spec, cudaStream_t s) { k_zero_dc<<<1, 1, 0, s>>>(spec); }
 
 }  // namespace bps

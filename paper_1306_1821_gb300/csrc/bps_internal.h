@@ -11,58 +11,65 @@ namespace bps {
 struct Fields;
 
 // Launchers of the field passes of one grid size (bps_passes.cu).
+// Launchers of the field passes of one grid size (bps_passes.cu).  The `nch`
+// argument is the number of chains of a batch (gridDim.y); a single-chain
+// operation passes fields already moved to its chain and nch = 1.
 struct PassTable {
   int N, zp, F, x_tiles, z_tiles;
-  void (*x_init)(const Fields&, int region, cudaStream_t);
-  void (*x_leap)(const Fields&, int first, cudaStream_t);
-  void (*x_final)(const Fields&, int region, cudaStream_t);
-  void (*x_inv)(const Fields&, int src_buf, float2* dst, cudaStream_t);   // src_buf -1: current state
-  void (*x_fwd)(const Fields&, int src_buf, float2* dst, cudaStream_t);   // dst NULL: current state
-  void (*x_grad)(const Fields&, float2* dst, int region, cudaStream_t);
-  void (*x_jinv)(const Fields&, cudaStream_t);
-  void (*x_jgrad)(const Fields&, int region, cudaStream_t);
-  void (*x_scale)(const Fields&, cudaStream_t);
-  void (*x_binpow)(const Fields&, int region, cudaStream_t);
-  void (*y_fwd)(const Fields&, int buf, cudaStream_t);
-  void (*y_inv)(const Fields&, int buf, cudaStream_t);
-  void (*z_grad)(const Fields&, int region, cudaStream_t);
-  void (*z_noise)(const Fields&, uint64_t seed, cudaStream_t);
-  void (*z_r2c)(const Fields&, const float* rin, float2* dst, cudaStream_t);
-  void (*z_c2r)(const Fields&, const float2* src, float* rout, cudaStream_t);
-  void (*z_sums)(const Fields&, int region, cudaStream_t);
+  void (*x_init)(const Fields&, int region, int nch, cudaStream_t);
+  void (*x_leap)(const Fields&, int first, int nch, cudaStream_t);
+  void (*x_final)(const Fields&, int region, int nch, cudaStream_t);
+  void (*x_inv)(const Fields&, int src_buf, float2* dst, int nch, cudaStream_t);   // src_buf -1: current state; dst NULL: W
+  void (*x_fwd)(const Fields&, int src_buf, float2* dst, int nch, cudaStream_t);   // dst NULL: current state
+  void (*x_grad)(const Fields&, float2* dst, int region, int nch, cudaStream_t);
+  void (*x_jinv)(const Fields&, int nch, cudaStream_t);
+  void (*x_jgrad)(const Fields&, int region, int nch, cudaStream_t);
+  void (*x_scale)(const Fields&, int nch, cudaStream_t);
+  void (*x_binpow)(const Fields&, int region, int nch, cudaStream_t);
+  void (*y_fwd)(const Fields&, int buf, int nch, cudaStream_t);
+  void (*y_inv)(const Fields&, int buf, int nch, cudaStream_t);
+  void (*z_grad)(const Fields&, int region, int nch, cudaStream_t);
+  void (*z_noise)(const Fields&, int nch, cudaStream_t);
+  void (*z_r2c)(const Fields&, const float* rin, float2* dst, cudaStream_t);   // one chain
+  void (*z_c2r)(const Fields&, const float2* src, float* rout, cudaStream_t);  // one chain
+  void (*z_sums)(const Fields&, int region, int nch, cudaStream_t);
 };
 
 bool pass_table(int N, PassTable* out);
-void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, cudaStream_t s);
+void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int nch, cudaStream_t s);
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
                  int stride, int blocks, cudaStream_t s);
 void launch_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
                          uint64_t* out, cudaStream_t s);
 void launch_voxel_normals(uint64_t seed, uint64_t it, size_t n, float* out, cudaStream_t s);
 
-// Scalar stages of the Gibbs scan (bps_draws.cu).
+// Scalar stages of the Gibbs scan (bps_draws.cu).  Chain j of a batch uses
+// ds + j and part + j * cstride (blockIdx.y); per-chain constants (seed, cell
+// volume, number of subsamples) live in its DevState.
 struct ScalarArgs {
   DevState* ds;
   const double* part;
   int stride;
-  int n_bins, n_sub, n_mass;
-  double Vc, inv_nv, alpha, eps_max, jeps_max;
-  uint64_t seed;
+  long long cstride;
+  int n_bins, max_sub, n_mass;
+  double inv_nv, alpha, eps_max, jeps_max;
   int fixed_bias;
 };
-void launch_move_begin(const ScalarArgs& a, cudaStream_t s);
-void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz,
+void launch_move_begin(const ScalarArgs& a, int nch, cudaStream_t s);
+void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz, int nch,
                      cudaStream_t s);
-void launch_power(const ScalarArgs& a, int region, int nx, int draw, cudaStream_t s);
-void launch_bias_nbar(const ScalarArgs& a, int region, int nz, cudaStream_t s);
-void launch_abar(const ScalarArgs& a, int region, int nblk, cudaStream_t s);
-void launch_jump_begin(const ScalarArgs& a, cudaStream_t s);
-void launch_jump_reduce(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, cudaStream_t s);
-void launch_jump_update(const ScalarArgs& a, int kind, cudaStream_t s);
+void launch_power(const ScalarArgs& a, int region, int nx, int draw, int nch, cudaStream_t s);
+void launch_bias_nbar(const ScalarArgs& a, int region, int nz, int nch, cudaStream_t s);
+void launch_abar(const ScalarArgs& a, int region, int nblk, int nch, cudaStream_t s);
+void launch_jump_begin(const ScalarArgs& a, int nch, cudaStream_t s);
+void launch_jump_reduce(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, int nch, cudaStream_t s);
+void launch_jump_update(const ScalarArgs& a, int kind, int nch, cudaStream_t s);
 void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, double scale, double* out_dev,
                       cudaStream_t s);
-void launch_record(const ScalarArgs& a, double* rec_dev, cudaStream_t s);
-void launch_advance(DevState* ds, cudaStream_t s);
+void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long iter_stride, int chain0, int nch,
+                   cudaStream_t s);
+void launch_advance(DevState* ds, int nch, cudaStream_t s);
+void launch_reset_rec(DevState* ds, int nch, cudaStream_t s);
 void launch_zero_dc(float2* spec, cudaStream_t s);
 
 enum JumpKind { J_FIRST = 0, J_MID = 1, J_LAST = 2 };

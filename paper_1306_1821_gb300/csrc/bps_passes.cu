@@ -60,7 +60,8 @@ __device__ __forceinline__ const float2* buf_ptr(const Fields& fp, int b) {
 
 // ------------------------------------------------------------------ x pass
 template <int N, int MODE>
-__global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fields fp, XArgs xa) {
+__global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fields fp0, XArgs xa) {
+  const Fields fp = at_chain(fp0, blockIdx.y);
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT, NW = NT / 32;
   constexpr bool BINNED = (MODE == X_JGRAD || MODE == X_BINPOW);
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
       }
     }
     fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
-    float2* out = (MODE == X_INV) ? xa.dst : fp.W;
+    float2* out = (MODE == X_INV && xa.dst) ? xa.dst : fp.W;   // no destination: this chain's W
     if (ja < R1) {
 #pragma unroll
       for (int b = 0; b < R2; ++b) out[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
@@ -359,7 +360,8 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
 
 // ------------------------------------------------------------------ y pass
 template <int N, int DIR>
-__global__ void __launch_bounds__(Cfg<N>::NT) k_ypass(Fields fp, int buf) {
+__global__ void __launch_bounds__(Cfg<N>::NT) k_ypass(Fields fp0, int buf) {
+  const Fields fp = at_chain(fp0, blockIdx.y);
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT;
   __shared__ float2 s_tw[N];
@@ -420,7 +422,8 @@ struct ZSmem {
 };
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
+__global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
+  const Fields fp = at_chain(fp0, blockIdx.y);
   using C = Cfg<N>;
   using L = ZSmem<N, MODE>;
   constexpr int R1 = C::R1, R2 = C::R2, H = C::H, ZP = C::ZP, NTZ = C::NTZ;
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
     float* sr = reinterpret_cast<float*>(s_buf);
     if constexpr (MODE == Z_NOISE) {
       const unsigned long long it = ds->iteration;
-      const uint64_t key = za.seed;
+      const uint64_t key = ds->seed;
       const unsigned long long blk0 = (unsigned long long)(L0 * N) / 8;
       for (int q = t; q < LINES * N / 8; q += NTZ) {
         P4 r = philox(blk0 + q, it, ST_MOMENTUM, 0, key);
@@ -543,7 +546,8 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
     }
     if constexpr (MODE == Z_SUMS) {
       const long long nv = (long long)N * N * N;
-      for (int l = 0; l < fp.n_sub; ++l) {
+      const int nsub = ds->nsub;
+      for (int l = 0; l < nsub; ++l) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (f < 16) {
           const uint16_t* cn = fp.cnt + l * nv;
@@ -600,7 +604,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
     }
   }
   __syncthreads();
-  float2* dst = (MODE == Z_GRAD) ? fp.W : za.dst;
+  float2* dst = (MODE == Z_GRAD) ? fp.W : (MODE == Z_NOISE) ? fp.ph : za.dst;
   for (int i = t; i < LINES * (H + 1); i += NTZ) {
     const int l = i / (H + 1), k = i - l * (H + 1);
     const int f = l >> 1;
@@ -616,11 +620,13 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp, ZArgs za) {
 // ------------------------------------------------------------------ voxel kernels
 // a_i = sum_l b_l^2 Nbar_l R^l_i,  c_i = sum_l b_l (N^l_i - Nbar_l R^l_i)  (Eq. Wiener_Posterior_force);
 // the counts are zero wherever R = 0 (checked by set_data), so no mask is needed.
-__global__ void __launch_bounds__(256) k_rebuild(Fields fp, long long nv, int region) {
+__global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int region) {
+  const Fields fp = at_chain(fp0, blockIdx.y);
   __shared__ float s_a[MAXS], s_b[MAXS], s_bn[MAXS];
   __shared__ double s_red[32];
   DevState* ds = fp.ds;
-  if (threadIdx.x < fp.n_sub) {
+  const int nsub = ds->nsub;
+  if (threadIdx.x < nsub) {
     const double b = ds->b[threadIdx.x], nb = ds->nbar[threadIdx.x];
     s_a[threadIdx.x] = (float)(b * b * nb);
     s_b[threadIdx.x] = (float)b;
@@ -631,7 +637,7 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp, long long nv, int re
   const long long n4 = nv / 4;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Cc = A;
-    for (int l = 0; l < fp.n_sub; ++l) {
+    for (int l = 0; l < nsub; ++l) {
       const float4 r = reinterpret_cast<const float4*>(fp.R + l * nv)[i];
       const ushort4 n = reinterpret_cast<const ushort4*>(fp.cnt + l * nv)[i];
       const float ka = s_a[l], kb = s_b[l], kbn = s_bn[l];
@@ -712,18 +718,17 @@ template <int N>
 struct Launch {
   using C = Cfg<N>;
   template <int M>
-  static void x(const Fields& fp, const XArgs& xa, cudaStream_t s) {
-    k_xpass<N, M><<<C::TILES, C::NT, 0, s>>>(fp, xa);
+  static void x(const Fields& fp, const XArgs& xa, int nch, cudaStream_t s) {
+    k_xpass<N, M><<<dim3(C::TILES, nch), C::NT, 0, s>>>(fp, xa);
   }
   template <int D>
-  static void y(const Fields& fp, int buf, cudaStream_t s) {
-    k_ypass<N, D><<<C::TILES, C::NT, 0, s>>>(fp, buf);
+  static void y(const Fields& fp, int buf, int nch, cudaStream_t s) {
+    k_ypass<N, D><<<dim3(C::TILES, nch), C::NT, 0, s>>>(fp, buf);
   }
   template <int M>
-  static void z(const Fields& fp, const ZArgs& za, cudaStream_t s) {
-    k_zpass<N, M><<<C::ZTILES, C::NTZ, ZSmem<N, M>::BYTES, s>>>(fp, za);
+  static void z(const Fields& fp, const ZArgs& za, int nch, cudaStream_t s) {
+    k_zpass<N, M><<<dim3(C::ZTILES, nch), C::NTZ, ZSmem<N, M>::BYTES, s>>>(fp, za);
   }
-
   template <int M>
   static void zattr() {
     cudaFuncSetAttribute(k_zpass<N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZSmem<N, M>::BYTES);
@@ -744,23 +749,23 @@ static PassTable make_table() {
   T.F = C::F;
   T.x_tiles = C::TILES;
   T.z_tiles = C::ZTILES;
-  T.x_init = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_INIT>(f, XArgs{-1, nullptr, 0, region}, s); };
-  T.x_leap = [](const Fields& f, int first, cudaStream_t s) { L::template x<X_LEAP>(f, XArgs{-1, nullptr, first, -1}, s); };
-  T.x_final = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_FINAL>(f, XArgs{-1, nullptr, 0, region}, s); };
-  T.x_inv = [](const Fields& f, int src, float2* dst, cudaStream_t s) { L::template x<X_INV>(f, XArgs{src, dst, 0, -1}, s); };
-  T.x_fwd = [](const Fields& f, int src, float2* dst, cudaStream_t s) { L::template x<X_FWD>(f, XArgs{src, dst, 0, -1}, s); };
-  T.x_grad = [](const Fields& f, float2* dst, int region, cudaStream_t s) { L::template x<X_GRAD>(f, XArgs{-1, dst, 0, region}, s); };
-  T.x_jinv = [](const Fields& f, cudaStream_t s) { L::template x<X_JINV>(f, XArgs{-1, nullptr, 0, -1}, s); };
-  T.x_jgrad = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_JGRAD>(f, XArgs{-1, nullptr, 0, region}, s); };
-  T.x_scale = [](const Fields& f, cudaStream_t s) { L::template x<X_SCALE>(f, XArgs{-1, nullptr, 0, -1}, s); };
-  T.x_binpow = [](const Fields& f, int region, cudaStream_t s) { L::template x<X_BINPOW>(f, XArgs{-1, nullptr, 0, region}, s); };
-  T.y_fwd = [](const Fields& f, int buf, cudaStream_t s) { L::template y<FWD>(f, buf, s); };
-  T.y_inv = [](const Fields& f, int buf, cudaStream_t s) { L::template y<INV>(f, buf, s); };
-  T.z_grad = [](const Fields& f, int region, cudaStream_t s) { L::template z<Z_GRAD>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, s); };
-  T.z_noise = [](const Fields& f, uint64_t seed, cudaStream_t s) { L::template z<Z_NOISE>(f, ZArgs{nullptr, f.ph, nullptr, nullptr, -1, seed}, s); };
-  T.z_r2c = [](const Fields& f, const float* rin, float2* dst, cudaStream_t s) { L::template z<Z_R2C>(f, ZArgs{nullptr, dst, rin, nullptr, -1, 0}, s); };
-  T.z_c2r = [](const Fields& f, const float2* src, float* rout, cudaStream_t s) { L::template z<Z_C2R>(f, ZArgs{src, nullptr, nullptr, rout, -1, 0}, s); };
-  T.z_sums = [](const Fields& f, int region, cudaStream_t s) { L::template z<Z_SUMS>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, s); };
+  T.x_init = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_INIT>(f, XArgs{-1, nullptr, 0, region}, n, s); };
+  T.x_leap = [](const Fields& f, int first, int n, cudaStream_t s) { L::template x<X_LEAP>(f, XArgs{-1, nullptr, first, -1}, n, s); };
+  T.x_final = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_FINAL>(f, XArgs{-1, nullptr, 0, region}, n, s); };
+  T.x_inv = [](const Fields& f, int src, float2* dst, int n, cudaStream_t s) { L::template x<X_INV>(f, XArgs{src, dst, 0, -1}, n, s); };
+  T.x_fwd = [](const Fields& f, int src, float2* dst, int n, cudaStream_t s) { L::template x<X_FWD>(f, XArgs{src, dst, 0, -1}, n, s); };
+  T.x_grad = [](const Fields& f, float2* dst, int region, int n, cudaStream_t s) { L::template x<X_GRAD>(f, XArgs{-1, dst, 0, region}, n, s); };
+  T.x_jinv = [](const Fields& f, int n, cudaStream_t s) { L::template x<X_JINV>(f, XArgs{-1, nullptr, 0, -1}, n, s); };
+  T.x_jgrad = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_JGRAD>(f, XArgs{-1, nullptr, 0, region}, n, s); };
+  T.x_scale = [](const Fields& f, int n, cudaStream_t s) { L::template x<X_SCALE>(f, XArgs{-1, nullptr, 0, -1}, n, s); };
+  T.x_binpow = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_BINPOW>(f, XArgs{-1, nullptr, 0, region}, n, s); };
+  T.y_fwd = [](const Fields& f, int buf, int n, cudaStream_t s) { L::template y<FWD>(f, buf, n, s); };
+  T.y_inv = [](const Fields& f, int buf, int n, cudaStream_t s) { L::template y<INV>(f, buf, n, s); };
+  T.z_grad = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_GRAD>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
+  T.z_noise = [](const Fields& f, int n, cudaStream_t s) { L::template z<Z_NOISE>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, -1, 0}, n, s); };
+  T.z_r2c = [](const Fields& f, const float* rin, float2* dst, cudaStream_t s) { L::template z<Z_R2C>(f, ZArgs{nullptr, dst, rin, nullptr, -1, 0}, 1, s); };
+  T.z_c2r = [](const Fields& f, const float2* src, float* rout, cudaStream_t s) { L::template z<Z_C2R>(f, ZArgs{src, nullptr, nullptr, rout, -1, 0}, 1, s); };
+  T.z_sums = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_SUMS>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
   return T;
 }
 
@@ -777,8 +782,8 @@ bool pass_table(int N, PassTable* out) {
   }
 }
 
-void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, cudaStream_t s) {
-  k_rebuild<<<blocks, 256, 0, s>>>(fp, nv, region);
+void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int nch, cudaStream_t s) {
+  k_rebuild<<<dim3(blocks, nch), 256, 0, s>>>(fp, nv, region);
 }
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
                  int stride, int blocks, cudaStream_t s) {

@@ -35,8 +35,28 @@ struct Fields {
   const float2* tw;       // W_N^j = exp(-2 pi i j / N), j < N (FP64-rounded)
   float inv_nv;           // 1 / N^3
   int mass_mode;
-  int n_sm;               // streaming multiprocessors (grid of the persistent passes)
+  int n_sm;               // streaming multiprocessors
+  // chains of one batch: chain j's buffers sit at j times these strides
+  long long spec_stride;  // complex elements per half spectrum
+  long long real_stride;  // voxels per real field
+  long long data_stride;  // elements per chain of counts / response (max subsamples x voxels)
+  long long part_cstride; // doubles of partial sums per chain
 };
+
+// The fields of chain `ch` of a batch (blockIdx.y of the field passes).
+__host__ __device__ __forceinline__ Fields at_chain(Fields f, int ch) {
+  f.dh[0] += ch * f.spec_stride;
+  f.dh[1] += ch * f.spec_stride;
+  f.ph += ch * f.spec_stride;
+  f.W += ch * f.spec_stride;
+  f.a += ch * f.real_stride;
+  f.c += ch * f.real_stride;
+  f.cnt += ch * f.data_stride;
+  f.R += ch * f.data_stride;
+  f.ds += ch;
+  f.part += ch * f.part_cstride;
+  return f;
+}
 
 enum { MAP_COL = 0, MAP_ROW = 1 };
 

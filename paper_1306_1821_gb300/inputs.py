@@ -112,13 +112,16 @@ def bin_centre_spectrum(N, box, n_bins):
     return true_spectrum(2.0 * np.pi * nc / box, N, box)
 
 
-def response(N, box, f_sky, radial, r0=350.0):
-    """Survey response R (float32 [N]^3): spherical cap times radial selection."""
+def response(N, box, f_sky, radial, r0=350.0, axis=(0.0, 0.0, 1.0)):
+    """Survey response R (float32 [N]^3): spherical cap about `axis` times radial selection."""
     dx = box / N
     c = (np.arange(N) + 0.5) * dx - box / 2.0
     x, y, z = np.meshgrid(c, c, c, indexing="ij")
     r = np.sqrt(x * x + y * y + z * z)
-    cos_t = np.where(r > 0, z / np.maximum(r, 1e-300), 1.0)
+    ax = np.asarray(axis, dtype=np.float64)
+    ax = ax / np.linalg.norm(ax)
+    proj = ax[0] * x + ax[1] * y + ax[2] * z
+    cos_t = np.where(r > 0, proj / np.maximum(r, 1e-300), 1.0)
     cap = cos_t >= 1.0 - 2.0 * f_sky
     rmax = box / 2.0
     if radial == "linear":
@@ -140,7 +143,7 @@ def make_survey(wl: Workload, seed=None):
     amp = np.sqrt(true_spectrum(k, N, wl.box) / vc)
     amp[0, 0, 0] = 0.0
     delta = np.fft.irfftn(amp * np.fft.rfftn(xi), s=(N, N, N), axes=(0, 1, 2))
-    R1 = response(N, wl.box, wl.f_sky, wl.radial, wl.r0)
+    R1 = response(N, wl.box, wl.f_sky, wl.radial, wl.r0, wl.extra.get("axis", (0.0, 0.0, 1.0)))
     R = np.broadcast_to(R1, (wl.n_sub, N, N, N)).copy()
     counts = np.empty((wl.n_sub, N, N, N), dtype=np.int32)
     for l in range(wl.n_sub):
@@ -160,3 +163,25 @@ def random_spectrum(N, n_bins, seed, scale=1.0):
     rng = np.random.Generator(np.random.PCG64(seed))
     x = rng.standard_normal((N, N, N)) * scale
     return np.fft.rfftn(x)
+
+
+def batch_workloads(sizes=(32, 64, 96), per_size=32, seed0=1000):
+    """Many small independent surveys: per_size chains of each grid size, box
+    L = 500 N / 32 Mpc/h (the cell size of the 32^3 survey), a spherical cap of
+    20-60% of the sky about a random direction with linear radial fall-off to
+    L/2, 1-4 luminosity subsamples (the first entries of the six-subsample
+    lists) and 16 k bins; chain j draws its mock from seed seed0 + j."""
+    out = []
+    j = 0
+    for N in sizes:
+        for _ in range(per_size):
+            rng = np.random.Generator(np.random.PCG64(seed0 + j))
+            f_sky = float(rng.uniform(0.2, 0.6))
+            n_sub = int(rng.integers(1, 5))
+            v = rng.standard_normal(3)
+            wl = Workload(f"batch{j}", N, 500.0 * N / 32.0, 16, SIX_B[:n_sub], _six_nbar()[:n_sub], f_sky,
+                          "linear", n_leapfrog=10, eps_max=0.1, seed=seed0 + j,
+                          extra={"axis": tuple(v / np.linalg.norm(v))})
+            out.append(wl)
+            j += 1
+    return out
