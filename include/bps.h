@@ -180,11 +180,59 @@ bps_status bps_batch_gibbs_iterate(bps_ctx* batch, int n_iter, double* chain_out
 int bps_batch_record_len(const bps_ctx* batch);
 int bps_batch_record_slot(const bps_ctx* batch, int chain);
 
+/* Posterior statistics of the density modes, the training targets of the
+ * mass preconditioner: n_moves HMC moves of every chain (ctx single or batch;
+ * the power spectrum, biases and normalisations stay fixed), then per chain and
+ * mass bin j (n_mass_bins linear bins in |n|, as for P) out receives
+ *   V_j    = mean over the bin's full-grid modes of Var(delta_k) / N^3 and
+ *   Mbar_j = mean of the diagonal mass V_cell / P_k + abar over the same modes,
+ * at out[slot * 2 n_mass_bins + j] and out[slot * 2 n_mass_bins + n_mass_bins + j]
+ * (host; slot 0 for a single context, bps_batch_record_slot(j) for a batch).
+ * The variance estimate is the sample variance of the chain's states.  Also
+ * installs n_mass_bins as the mass-bin layout (as bps_set_mass_scale does). */
+bps_status bps_mass_stats(bps_ctx* ctx, int n_moves, int n_mass_bins, double* out);
+
+/* Binned power of the survey window, a feature of the mass preconditioner:
+ * out[slot * n_bins + m] = sigma_m of a / abar, with a = sum_l b_l^2 Nbar_l R^l
+ * the local curvature of Eq. Wiener_Posterior_force and sigma_m as in
+ * bps_sample_power (host; slots as in bps_mass_stats). */
+bps_status bps_window_power(bps_ctx* ctx, double* out);
+
 /* Per-bin multipliers s_m of the diagonal mass for mass_mode = 1 (a
  * preconditioner choice: the mass affects efficiency, not validity,
  * Sec. 4.1.2).  scales [n_mass_bins] host, 1 <= n_mass_bins <= 64, bins
  * linear in |n| as for P. */
 bps_status bps_set_mass_scale(bps_ctx* ctx, int n_mass_bins, const double* scales);
+
+/* ---- the mass-preconditioner network ----
+ * A multilayer perceptron (ReLU hidden layers, linear output) that maps binned
+ * features of a problem to per-bin log multipliers of the diagonal mass (for
+ * bps_set_mass_scale).  The paper keeps the Fourier diagonal of Eq.
+ * Mass_matrix and notes the mass changes efficiency only (Sec. 4.1.2); the
+ * network is this library's way to choose better multipliers.  Matrix products
+ * use BF16 operands with FP32 accumulation on the tensor cores; parameters and
+ * Adam moments are FP32.  Parameters are one FP32 vector, layer by layer: W_l
+ * [n_l][n_{l+1}] row-major, then b_l [n_{l+1}].  Loss: mean squared error. */
+typedef struct bps_mlp bps_mlp;
+/* sizes[0..n_layers]: input, hidden..., output widths (each 1..512; 1..4 layers). */
+bps_status bps_mlp_create(int n_layers, const int* sizes, void* cuda_stream, bps_mlp** out);
+size_t bps_mlp_num_params(const bps_mlp* net);
+bps_status bps_mlp_set_params(bps_mlp* net, const float* params);   /* host; resets Adam */
+bps_status bps_mlp_get_params(bps_mlp* net, float* params);         /* host */
+/* y_dev [batch][n_out] = network(x_dev [batch][n_in]) (device arrays). */
+bps_status bps_mlp_forward(bps_mlp* net, int batch, const float* x_dev, float* y_dev);
+/* Loss and parameter gradients for one batch; loss (host double) and grads
+ * (host float [num_params]) may be NULL.  Keeps the gradients for bps_mlp_adam_step. */
+bps_status bps_mlp_loss_grad(bps_mlp* net, int batch, const float* x_dev, const float* t_dev, double* loss,
+                             float* grads);
+/* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected) with the last gradients. */
+bps_status bps_mlp_adam_step(bps_mlp* net, float lr);
+/* `steps` Adam steps on minibatches of `batch` rows drawn with replacement from
+ * the n_examples rows of x_dev / t_dev (Philox key `seed`); last_loss (host, may
+ * be NULL) receives the loss of the last minibatch. */
+bps_status bps_mlp_train(bps_mlp* net, int n_examples, const float* x_dev, const float* t_dev, int batch,
+                         int steps, float lr, uint64_t seed, double* last_loss);
+void bps_mlp_destroy(bps_mlp* net);
 
 /* ---- building blocks of the path, for verification ---- */
 

@@ -70,6 +70,18 @@ _SIGS = {
     "bps_batch_gibbs_iterate": ([_P, ctypes.c_int, _D], ctypes.c_int),
     "bps_batch_record_len": ([_P], ctypes.c_int),
     "bps_batch_record_slot": ([_P, ctypes.c_int], ctypes.c_int),
+    "bps_mlp_create": ([ctypes.c_int, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "bps_mlp_num_params": ([_P], ctypes.c_size_t),
+    "bps_mlp_set_params": ([_P, _P], ctypes.c_int),
+    "bps_mlp_get_params": ([_P, _P], ctypes.c_int),
+    "bps_mlp_forward": ([_P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "bps_mlp_loss_grad": ([_P, ctypes.c_int, _P, _P, _D, _P], ctypes.c_int),
+    "bps_mlp_adam_step": ([_P, ctypes.c_float], ctypes.c_int),
+    "bps_mlp_train": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _D],
+                      ctypes.c_int),
+    "bps_mlp_destroy": ([_P], None),
+    "bps_mass_stats": ([_P, ctypes.c_int, ctypes.c_int, _D], ctypes.c_int),
+    "bps_window_power": ([_P, _D], ctypes.c_int),
     "bps_bin_power_noalloc": ([ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "bps_destroy": ([_P], None),
 }
@@ -305,6 +317,90 @@ def bps_batch_gibbs_iterate(ctx, n_iter, n_chains=None):
     out = np.zeros(int(n_iter) * n_chains * rl)
     _check(ctx, load().bps_batch_gibbs_iterate(ctx, int(n_iter), out.ctypes.data_as(_D)))
     return out.reshape(int(n_iter), n_chains, rl)
+
+
+class MLP:
+    """The mass-preconditioner network (device parameters; FP32 host views)."""
+
+    def __init__(self, sizes, stream=None):
+        self.sizes = [int(x) for x in sizes]
+        arr = np.ascontiguousarray(self.sizes, dtype=np.int32)
+        self.ptr = _P()
+        _check(None, load().bps_mlp_create(len(sizes) - 1, arr.ctypes.data_as(_P), _stream_ptr(stream),
+                                           ctypes.byref(self.ptr)))
+        self.n_params = int(load().bps_mlp_num_params(self.ptr))
+
+    def _chk(self, st):
+        _check(None, st)
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.n_params
+        self._chk(load().bps_mlp_set_params(self.ptr, a.ctypes.data_as(_P)))
+
+    def get_params(self):
+        a = np.zeros(self.n_params, dtype=np.float32)
+        self._chk(load().bps_mlp_get_params(self.ptr, a.ctypes.data_as(_P)))
+        return a
+
+    def forward(self, x, y):
+        self._chk(load().bps_mlp_forward(self.ptr, int(x.shape[0]), _dptr(x), _dptr(y)))
+
+    def loss_grad(self, x, t):
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        self._chk(load().bps_mlp_loss_grad(self.ptr, int(x.shape[0]), _dptr(x), _dptr(t), ctypes.byref(loss),
+                                           g.ctypes.data_as(_P)))
+        return loss.value, g
+
+    def adam_step(self, lr):
+        self._chk(load().bps_mlp_adam_step(self.ptr, float(lr)))
+
+    def train(self, x, t, batch, steps, lr, seed=0):
+        loss = ctypes.c_double(0.0)
+        self._chk(load().bps_mlp_train(self.ptr, int(x.shape[0]), _dptr(x), _dptr(t), int(batch), int(steps),
+                                       float(lr), int(seed), ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.ptr is not None:
+            load().bps_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def flatten_params(params):
+    """oracle-style [W1, b1, W2, b2, ...] (float64) -> the library's flat FP32 vector."""
+    return np.concatenate([np.asarray(p, dtype=np.float32).ravel() for p in params])
+
+
+def unflatten_params(flat, sizes):
+    out, off = [], 0
+    for n_in, n_out in zip(sizes[:-1], sizes[1:]):
+        out.append(np.asarray(flat[off:off + n_in * n_out], dtype=np.float64).reshape(n_in, n_out))
+        off += n_in * n_out
+        out.append(np.asarray(flat[off:off + n_out], dtype=np.float64))
+        off += n_out
+    return out
+
+
+def bps_mass_stats(ctx, n_moves, n_mass_bins, n_slots=1):
+    """(V [n_slots, n_mass], Mbar [n_slots, n_mass]) of the chains' density modes."""
+    out = np.zeros(n_slots * 2 * n_mass_bins)
+    _check(ctx, load().bps_mass_stats(ctx, int(n_moves), int(n_mass_bins), out.ctypes.data_as(_D)))
+    out = out.reshape(n_slots, 2, n_mass_bins)
+    return out[:, 0], out[:, 1]
+
+
+def bps_window_power(ctx, n_bins, n_slots=1):
+    out = np.zeros(n_slots * n_bins)
+    _check(ctx, load().bps_window_power(ctx, out.ctypes.data_as(_D)))
+    return out.reshape(n_slots, n_bins)
 
 
 def bps_version():

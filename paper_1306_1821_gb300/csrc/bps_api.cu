@@ -40,6 +40,7 @@ struct bps_ctx {
   float2* dh[2] = {nullptr, nullptr};
   float2* ph = nullptr;
   float2* W = nullptr;
+  float2* acc = nullptr;      // running sum of the state (bps_batch_mass_stats), allocated on first use
   float* a = nullptr;
   float* c = nullptr;
   uint16_t* cnt = nullptr;
@@ -126,6 +127,7 @@ Fields fields(bps_ctx* c) {
   f.dh[1] = c->dh[1];
   f.ph = c->ph;
   f.W = c->W;
+  f.acc = c->acc;
   f.a = c->a;
   f.c = c->c;
   f.cnt = c->cnt;
@@ -480,6 +482,7 @@ void free_all(bps_ctx* c) {
   cudaFree(c->dh[1]);
   cudaFree(c->ph);
   cudaFree(c->W);
+  cudaFree(c->acc);
   cudaFree(c->a);
   cudaFree(c->c);
   cudaFree(c->cnt);
@@ -801,6 +804,110 @@ bps_status run_iterations(bps_ctx* top, const std::vector<bps_ctx*>& groups, int
   }
   for (int i = 0; i < n_iter; ++i) CK(cudaGraphLaunch(top->graph, s));
   top->launches += (uint64_t)n_iter * top->graph_launches;
+  return BPS_OK;
+}
+
+// Posterior statistics of the density modes for the mass preconditioner: run
+// n_moves HMC moves of every chain (the hyperparameters stay fixed) and return,
+// per chain and mass bin j, V_j = mean over the bin's full-grid modes of
+// Var(delta_k) / N^3 (comparable with lambda_k = P/V_cell) and Mbar_j = mean of
+// the diagonal mass 1/lambda_k + abar over the same modes.
+bps_status mass_stats(bps_ctx* ctx, int n_moves, int n_mass, double* out, int out_stride, const std::vector<int>& slot) {
+  int thr[MAXB];
+  if (!bin_tables(ctx->N, n_mass, thr, nullptr))
+    return fail(ctx, BPS_EINVAL, "a mass bin holds no |n|^2 value; use fewer mass bins");
+  cudaStream_t s = ctx->stream;
+  const int B = ctx->batch;
+  if (!ctx->acc) {
+    if (cudaMalloc((void**)&ctx->acc, ctx->n_spec * sizeof(float2) * B) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BPS_ENOMEM, "accumulator allocation failed");
+    }
+  }
+  CK(cudaMemsetAsync(ctx->acc, 0, ctx->n_spec * sizeof(float2) * B, s));
+  std::vector<double> zero(MAXB, 0.0);
+  for (int ch = 0; ch < B; ++ch) {
+    bps_status st = ds_write_bytes(ctx, ch, DS_OFF(mthr), thr, sizeof(thr));
+    if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(mstat), zero.data(), MAXB * sizeof(double));
+    if (st != BPS_OK) return st;
+  }
+  const int keep_mass = ctx->n_mass;
+  ctx->n_mass = n_mass;   // the mass-bin table now has n_mass bins
+  drop_graph(ctx);
+  Fields f = fields(ctx);
+  ScalarArgs sa = scalars(ctx);
+  for (int i = 0; i < n_moves; ++i) {
+    bps_status st = hmc_move(ctx, true);
+    if (st != BPS_OK) return st;
+    ctx->pt.x_macc(f, region_offset(ctx, RG_BIN), B, s);
+    launch_mstat(sa, region_offset(ctx, RG_BIN), ctx->pt.x_tiles, n_mass, 0, B, s);
+    LAUNCHED(ctx, 2);
+  }
+  ctx->pt.x_mmean(f, region_offset(ctx, RG_BIN), B, s);
+  launch_mstat(sa, region_offset(ctx, RG_BIN), ctx->pt.x_tiles, n_mass, 1, B, s);
+  LAUNCHED(ctx, 2);
+  CK(cudaStreamSynchronize(s));
+  (void)keep_mass;
+  // mode counts per (power bin, mass bin), full-grid weights
+  const int nb = ctx->cfg.n_bins, N = ctx->N, H = N / 2;
+  std::vector<double> cnt((size_t)nb * n_mass, 0.0), nj(n_mass, 0.0);
+  for (int ix = 0; ix < N; ++ix) {
+    const long long nx = ix <= H ? ix : ix - N;
+    for (int iy = 0; iy < N; ++iy) {
+      const long long ny = iy <= H ? iy : iy - N;
+      for (int iz = 0; iz <= H; ++iz) {
+        const long long n2 = nx * nx + ny * ny + (long long)iz * iz;
+        if (n2 == 0) continue;
+        const double w = (iz == 0 || iz == H) ? 1.0 : 2.0;
+        const int m = bin_of_host(n2, N, nb), j = bin_of_host(n2, N, n_mass);
+        cnt[(size_t)m * n_mass + j] += w;
+        nj[j] += w;
+      }
+    }
+  }
+  const double S = (double)n_moves, nv = (double)ctx->nv;
+  for (int ch = 0; ch < B; ++ch) {
+    std::vector<double> m1(MAXB), m2(MAXB), P(MAXB);
+    double abar = 0.0, vc = 0.0;
+    bps_status st = ds_read_bytes(ctx, ch, DS_OFF(mstat), m1.data(), MAXB * sizeof(double));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, ch, DS_OFF(mstat2), m2.data(), MAXB * sizeof(double));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, ch, DS_OFF(P), P.data(), MAXB * sizeof(double));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, ch, DS_OFF(abar), &abar, sizeof(double));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, ch, DS_OFF(vc), &vc, sizeof(double));
+    if (st != BPS_OK) return st;
+    double* o = out + (size_t)slot[ch] * out_stride;
+    for (int j = 0; j < n_mass; ++j) {
+      const double var = (m1[j] / S - m2[j] / (S * S)) / (nj[j] * nv);
+      double mb = 0.0;
+      for (int m = 0; m < nb; ++m) mb += cnt[(size_t)m * n_mass + j] * (vc / P[m] + abar);
+      o[j] = var;
+      o[n_mass + j] = mb / nj[j];
+    }
+  }
+  return BPS_OK;
+}
+
+// Binned power of the survey window: sigma_m of a / abar (the local curvature
+// a = sum_l b_l^2 Nbar_l R^l over its voxel mean), one chain per slot.
+bps_status window_power(bps_ctx* ctx, double* out, int out_stride, const std::vector<int>& slot) {
+  cudaStream_t s = ctx->stream;
+  const int nb = ctx->cfg.n_bins;
+  for (int ch = 0; ch < ctx->batch; ++ch) {
+    Fields f = fields_at(ctx, ch);
+    ctx->pt.z_r2c(f, f.a, f.W, s);
+    ctx->pt.y_fwd(f, BUF_W, 1, s);
+    ctx->pt.x_fwd(f, BUF_W, f.W, 1, s);
+    ctx->pt.x_wpow(f, region_offset(ctx, RG_BIN), 1, s);
+    launch_power(scalars_at(ctx, ch), region_offset(ctx, RG_BIN), ctx->pt.x_tiles, 0, 1, s);
+    LAUNCHED(ctx, 5);
+    std::vector<double> sig(MAXB);
+    double abar = 0.0;
+    bps_status st = ds_read_bytes(ctx, ch, DS_OFF(sigma), sig.data(), MAXB * sizeof(double));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, ch, DS_OFF(abar), &abar, sizeof(double));
+    if (st != BPS_OK) return st;
+    double* o = out + (size_t)slot[ch] * out_stride;
+    for (int m = 0; m < nb; ++m) o[m] = sig[m] / (abar * abar);
+  }
   return BPS_OK;
 }
 
@@ -1182,6 +1289,51 @@ bps_status bps_batch_gibbs_iterate(bps_ctx* batch, int n_iter, double* chain_out
     bps_status st = check_status(g);
     if (st != BPS_OK) {
       batch->err = g->err;
+      return st;
+    }
+  }
+  return BPS_OK;
+}
+
+bps_status bps_mass_stats(bps_ctx* ctx, int n_moves, int n_mass_bins, double* out) {
+  if (!ctx || !out) return fail(ctx, BPS_EINVAL, "null argument");
+  if (n_moves < 2) return fail(ctx, BPS_EINVAL, "n_moves must be >= 2");
+  if (n_mass_bins < 1 || n_mass_bins > MAXB) return fail(ctx, BPS_EINVAL, "n_mass_bins must be in 1..64");
+  if (!ctx->is_batch) {
+    bps_status st = need_data(ctx);
+    if (st != BPS_OK) return st;
+    st = mass_stats(ctx, n_moves, n_mass_bins, out, 2 * n_mass_bins, {0});
+    if (st != BPS_OK) return st;
+    return check_status(ctx);
+  }
+  for (bps_ctx* g : ctx->groups) {
+    for (int ch = 0; ch < g->batch; ++ch)
+      if (!g->have_data[ch]) return fail(ctx, BPS_ESTATE, "a chain has no data (bps_batch_set_chain)");
+    std::vector<int> slot(g->chain_id.begin(), g->chain_id.end());
+    bps_status st = mass_stats(g, n_moves, n_mass_bins, out, 2 * n_mass_bins, slot);
+    if (st == BPS_OK) st = check_status(g);
+    if (st != BPS_OK) {
+      ctx->err = g->err;
+      return st;
+    }
+  }
+  drop_graph(ctx);
+  return BPS_OK;
+}
+
+bps_status bps_window_power(bps_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, BPS_EINVAL, "null argument");
+  if (!ctx->is_batch) {
+    bps_status st = need_data(ctx);
+    if (st != BPS_OK) return st;
+    return window_power(ctx, out, ctx->cfg.n_bins, {0});
+  }
+  for (bps_ctx* g : ctx->groups) {
+    for (int ch = 0; ch < g->batch; ++ch)
+      if (!g->have_data[ch]) return fail(ctx, BPS_ESTATE, "a chain has no data (bps_batch_set_chain)");
+    bps_status st = window_power(g, out, ctx->cfg.n_bins, std::vector<int>(g->chain_id.begin(), g->chain_id.end()));
+    if (st != BPS_OK) {
+      ctx->err = g->err;
       return st;
     }
   }

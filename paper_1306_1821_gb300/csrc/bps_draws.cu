@@ -387,6 +387,18 @@ __global__ void k_reset_rec(DevState* ds) { ds[blockIdx.x].rec_idx = 0; }
 
 __global__ void k_zero_dc(float2* spec) { spec[0] = make_float2(0.f, 0.f); }
 
+// block j of chain blockIdx.y: sum of the per-tile partials of mass bin j
+__global__ void k_mstat(ScalarArgs a0, int region, int nblk, int final_) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  const double s = sum_partials(a.part + region + (size_t)j * a.stride, nblk, sh);
+  if (threadIdx.x == 0) {
+    if (final_) a.ds->mstat2[j] = s;
+    else a.ds->mstat[j] += s;
+  }
+}
+
 void launch_move_begin(const ScalarArgs& a, int nch, cudaStream_t s) { k_move_begin<<<dim3(1, nch), MAXB, 0, s>>>(a); }
 void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz, int nch,
                      cudaStream_t s) {
@@ -419,5 +431,8 @@ void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long 
 void launch_advance(DevState* ds, int nch, cudaStream_t s) { k_advance<<<nch, 1, 0, s>>>(ds); }
 void launch_reset_rec(DevState* ds, int nch, cudaStream_t s) { k_reset_rec<<<nch, 1, 0, s>>>(ds); }
 void launch_zero_dc(float2* spec, cudaStream_t s) { k_zero_dc<<<1, 1, 0, s>>>(spec); }
+void launch_mstat(const ScalarArgs& a, int region, int nblk, int n_mass, int final_, int nch, cudaStream_t s) {
+  k_mstat<<<dim3(n_mass, nch), 256, 0, s>>>(a, region, nblk, final_);
+}
 
 }  // namespace bps

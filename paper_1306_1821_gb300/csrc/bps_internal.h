@@ -26,6 +26,9 @@ struct PassTable {
   void (*x_jgrad)(const Fields&, int region, int nch, cudaStream_t);
   void (*x_scale)(const Fields&, int nch, cudaStream_t);
   void (*x_binpow)(const Fields&, int region, int nch, cudaStream_t);
+  void (*x_macc)(const Fields&, int region, int nch, cudaStream_t);    // acc += delta, mass-bin power
+  void (*x_mmean)(const Fields&, int region, int nch, cudaStream_t);   // mass-bin power of acc
+  void (*x_wpow)(const Fields&, int region, int nch, cudaStream_t);    // power-bin power of W
   void (*y_fwd)(const Fields&, int buf, int nch, cudaStream_t);
   void (*y_inv)(const Fields&, int buf, int nch, cudaStream_t);
   void (*z_grad)(const Fields&, int region, int nch, cudaStream_t);
@@ -70,6 +73,8 @@ void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long 
                    cudaStream_t s);
 void launch_advance(DevState* ds, int nch, cudaStream_t s);
 void launch_reset_rec(DevState* ds, int nch, cudaStream_t s);
+// per mass bin j < n_mass: DevState::mstat[j] += (or mstat2[j] =, when `final`) the sum of partials
+void launch_mstat(const ScalarArgs& a, int region, int nblk, int n_mass, int final_, int nch, cudaStream_t s);
 void launch_zero_dc(float2* spec, cudaStream_t s);
 
 enum JumpKind { J_FIRST = 0, J_MID = 1, J_LAST = 2 };

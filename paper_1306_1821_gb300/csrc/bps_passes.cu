@@ -25,7 +25,10 @@ enum XMode {
   X_JINV,       // W = IFFT_x(js_m delta)                (jump: field at theta)
   X_JGRAD,      // per-bin sum w Re(conj(FFT_x(W)) js_m delta)
   X_SCALE,      // delta *= js_m if the jump was accepted
-  X_BINPOW      // per-bin sum w |delta|^2
+  X_BINPOW,     // per-bin sum w |delta|^2
+  X_MACC,       // acc += delta; per mass-bin sum w |delta|^2
+  X_MMEAN,      // per mass-bin sum w |acc|^2
+  X_WPOW        // per-bin sum w |W|^2 (the power of whatever W holds)
 };
 
 enum ZMode { Z_GRAD = 0, Z_NOISE, Z_R2C, Z_C2R, Z_SUMS };
@@ -64,7 +67,8 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
   const Fields fp = at_chain(fp0, blockIdx.y);
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT, NW = NT / 32;
-  constexpr bool BINNED = (MODE == X_JGRAD || MODE == X_BINPOW);
+  constexpr bool BINNED = (MODE == X_JGRAD || MODE == X_BINPOW || MODE == X_MACC || MODE == X_MMEAN || MODE == X_WPOW);
+  constexpr bool MASSBINS = (MODE == X_MACC || MODE == X_MMEAN);
   __shared__ float2 s_tw[N];
   __shared__ __align__(16) float2 s_ex[N * F];
   __shared__ int s_thr[MAXB], s_mthr[MAXB];
@@ -334,10 +338,15 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
       if (act) {
         const int k = jc + R2 * d;
         const int nx = sgn_n<N>(k);
-        m = bin_of(nx * nx + n2yz, s_thr);
-        float2 x = dsel(fp, cur)[colo + (long long)k * T.rs];
+        m = bin_of(nx * nx + n2yz, MASSBINS ? s_mthr : s_thr);
+        const long long idx = colo + (long long)k * T.rs;
+        float2 x = (MODE == X_MMEAN) ? fp.acc[idx] : (MODE == X_WPOW) ? fp.W[idx] : dsel(fp, cur)[idx];
+        if constexpr (MODE == X_MACC) {
+          const float2 s0 = fp.acc[idx];
+          fp.acc[idx] = make_float2(s0.x + x.x, s0.y + x.y);
+        }
         if (m >= 0) {
-          if constexpr (MODE == X_BINPOW) {
+          if constexpr (MODE == X_BINPOW || MODE == X_MACC || MODE == X_MMEAN || MODE == X_WPOW) {
             e = wk * (x.x * x.x + x.y * x.y);
           } else {
             const float s = s_js[m];
@@ -759,6 +768,9 @@ static PassTable make_table() {
   T.x_jgrad = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_JGRAD>(f, XArgs{-1, nullptr, 0, region}, n, s); };
   T.x_scale = [](const Fields& f, int n, cudaStream_t s) { L::template x<X_SCALE>(f, XArgs{-1, nullptr, 0, -1}, n, s); };
   T.x_binpow = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_BINPOW>(f, XArgs{-1, nullptr, 0, region}, n, s); };
+  T.x_macc = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_MACC>(f, XArgs{-1, nullptr, 0, region}, n, s); };
+  T.x_mmean = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_MMEAN>(f, XArgs{-1, nullptr, 0, region}, n, s); };
+  T.x_wpow = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_WPOW>(f, XArgs{-1, nullptr, 0, region}, n, s); };
   T.y_fwd = [](const Fields& f, int buf, int n, cudaStream_t s) { L::template y<FWD>(f, buf, n, s); };
   T.y_inv = [](const Fields& f, int buf, int n, cudaStream_t s) { L::template y<INV>(f, buf, n, s); };
   T.z_grad = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_GRAD>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };

@@ -24,6 +24,7 @@ struct Fields {
   float2* dh[2];          // state double buffer (DevState::cur selects the current one)
   float2* ph;             // momentum half spectrum
   float2* W;              // work half spectrum
+  float2* acc;            // running sum of the state (posterior statistics), or NULL
   float* a;               // local curvature  a = sum_l b_l^2 Nbar_l R^l
   float* c;               // local drive      c = sum_l b_l (N^l - Nbar_l R^l)
   const uint16_t* cnt;    // counts [n_sub][N^3]
@@ -49,6 +50,7 @@ __host__ __device__ __forceinline__ Fields at_chain(Fields f, int ch) {
   f.dh[1] += ch * f.spec_stride;
   f.ph += ch * f.spec_stride;
   f.W += ch * f.spec_stride;
+  if (f.acc) f.acc += ch * f.spec_stride;
   f.a += ch * f.real_stride;
   f.c += ch * f.real_stride;
   f.cnt += ch * f.data_stride;
