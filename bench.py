@@ -412,6 +412,104 @@ def run_batch(args):
     return 0
 
 
+# ---------------------------------------------------------------- learned mass vs plain
+def pk_ess(rec, n_bins, N, secs):
+    """ESS of ln P_m per bin (Geyer) from a chain record, and ESS/s summaries over
+    the bins that lie inside the Nyquist sphere (|n| <= N/2); the corner bins
+    beyond it hold only shot-noise-dominated modes."""
+    import numpy as np
+
+    from paper_1306_1821_gb300 import diagnostics
+    P = rec[:, :n_bins]
+    ess = np.array([diagnostics.ess_geyer(np.log(P[:, m])) for m in range(n_bins)])
+    inside = [m for m in range(n_bins) if (m + 1) * math.sqrt(3.0) * N / 2 / n_bins <= N / 2]
+    return {"ess_per_bin": [round(float(e), 1) for e in ess],
+            "bins_inside_nyquist": inside,
+            "min_ess_per_s": float(ess[inside].min() / secs),
+            "median_ess_per_s": float(np.median(ess[inside]) / secs),
+            "iterations": int(len(rec)), "seconds": secs,
+            "mean_lnP": [round(float(v), 4) for v in np.log(P).mean(0)],
+            "sd_lnP": [round(float(v), 4) for v in np.log(P).std(0)]}
+
+
+def run_precond(args):
+    """P(k) effective samples per second of the full sampler on the 128^3
+    six-subsample survey, with the plain diagonal mass and with the trained
+    network mass.  The network (32 -> 128 -> 128 -> 64, BF16 operands) is
+    trained on the device on statistics of 64 surveys with random caps and
+    spectra, in two rounds (the second on chains that already move with the
+    first round's mass); the 128^3 survey itself is held out."""
+    import numpy as np
+    import torch
+
+    from paper_1306_1821_gb300 import bps, inputs, precond
+    if not os.path.exists(bps.LIB_PATH):
+        from paper_1306_1821_gb300 import build as b
+        b.build()
+    bps.load()
+    wl = inputs.WORKLOADS["survey128"]
+    n_mass, jeps = 64, 0.15
+    t0 = time.time()
+    probs = precond.random_problems(wl, 64, 5000, p_jitter=0.3)
+    F, T = precond.measure(probs, n_mass, n_moves=300, burn_in=100)
+    pc = precond.Preconditioner(F.shape[1], n_mass)
+    pc.fit(F, T, steps=2000, batch=64)
+    F2, T2 = precond.measure(probs, n_mass, n_moves=300, burn_in=100, sampler_mass=pc)
+    pc2 = precond.Preconditioner(F.shape[1], n_mass, seed=1)
+    loss = pc2.fit(F2, T2, steps=2000, batch=64)
+    train_s = time.time() - t0
+    delta, counts, R = inputs.make_survey(wl)
+    P0, b0, n0 = inputs.initial_state(wl)
+    cnt = torch.from_numpy(counts).cuda()
+    Rt = torch.from_numpy(R).cuda()
+    d32 = torch.from_numpy(delta.astype(np.float32)).cuda()
+    arms = {}
+    for arm in ("plain", "network"):
+        s = bps.Sampler(wl.N, wl.box, wl.n_sub, wl.n_bins, n_leapfrog=wl.n_leapfrog, eps_max=wl.eps_max, jump=1,
+                        jump_leapfrog=10, jump_eps_max=jeps, fixed_bias_index=0, seed=3)
+        bps.bps_set_data(s.ctx, cnt, Rt)
+        bps.bps_set_state(s.ctx, d32, P0, b0, n0, 0)
+        if arm == "network":
+            pc2.install(s.ctx)
+        bps.bps_gibbs_iterate(s.ctx, max(args.warmup, 300))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        rec = bps.bps_gibbs_iterate(s.ctx, args.ess_iters, s.rec_len)
+        e1.record()
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1000.0
+        r = pk_ess(rec, wl.n_bins, wl.N, secs)
+        r["hmc_acceptance"] = float(np.mean(rec[:, -1]))
+        r["ms_per_iteration"] = 1000.0 * secs / args.ess_iters
+        if arm == "network":
+            r["mass_scales_in_use"] = [round(float(v), 3) for v in bps.bps_get_mass_scale(s.ctx)]
+        s.close()
+        arms[arm] = r
+    line = {
+        "metric": "P(k) effective samples/s, learned mass vs plain diagonal mass (min over bins inside the "
+                  "Nyquist sphere)",
+        "value": arms["network"]["min_ess_per_s"],
+        "unit": "effective samples/s",
+        "n_gpus": 1, "steps": args.ess_iters, "warmup": max(args.warmup, 300),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
+        "data": "synthetic",
+        "config": {"workload": "survey128: 128^3 grid, L=750 Mpc/h, six subsamples, 25% sky, exp(-(r/350)^2) "
+                               "radial selection, 16 k bins, 10 leapfrog steps, jump on (10 steps, "
+                               f"eps_max {jeps}); network 32-128-128-64 trained on 64 random surveys, "
+                               "the survey itself held out"},
+        "plain": arms["plain"], "network": arms["network"],
+        "ratio_min_ess_per_s": arms["network"]["min_ess_per_s"] / arms["plain"]["min_ess_per_s"],
+        "ratio_median_ess_per_s": arms["network"]["median_ess_per_s"] / arms["plain"]["median_ess_per_s"],
+        "training": {"seconds": train_s, "examples": int(2 * len(F)), "final_minibatch_loss": loss},
+    }
+    print(json.dumps(line), flush=True)
+    pc.close()
+    pc2.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,7 +517,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96", "precond128"])
+    ap.add_argument("--ess-iters", type=int, default=20000,
+                    help="Gibbs iterations per arm of --workload precond128")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -427,6 +527,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batch96":
         return run_batch(args)
+    if args.workload == "precond128":
+        return run_precond(args)
     return run_ours(args)
 
 

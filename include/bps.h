@@ -189,7 +189,10 @@ int bps_batch_record_slot(const bps_ctx* batch, int chain);
  * at out[slot * 2 n_mass_bins + j] and out[slot * 2 n_mass_bins + n_mass_bins + j]
  * (host; slot 0 for a single context, bps_batch_record_slot(j) for a batch).
  * The variance estimate is the sample variance of the chain's states.  Also
- * installs n_mass_bins as the mass-bin layout (as bps_set_mass_scale does). */
+ * installs n_mass_bins as the mass-bin layout (as bps_set_mass_scale does).
+ * BPS_EINVAL if a mass bin holds no mode (the first bin must reach |n| = 1,
+ * so n_mass_bins < sqrt(3) N / 2), or if a network mass is installed and n_mass_bins
+ * differs from its output width. */
 bps_status bps_mass_stats(bps_ctx* ctx, int n_moves, int n_mass_bins, double* out);
 
 /* Binned power of the survey window, a feature of the mass preconditioner:
@@ -204,6 +207,29 @@ bps_status bps_window_power(bps_ctx* ctx, double* out);
  * linear in |n| as for P. */
 bps_status bps_set_mass_scale(bps_ctx* ctx, int n_mass_bins, const double* scales);
 
+/* Network mass: from now on, before every HMC move of every chain (ctx single
+ * or batch), the per-bin multipliers s_j of the diagonal mass are recomputed on
+ * the device by `net` from the chain's current state, inside the Gibbs
+ * iteration's launch sequence (no host round trip):
+ *   z = clamp((f - feat_mean) / feat_std, -4, 4),
+ *   f = [ln P_0 .. ln P_{n_bins-1}, ln W_0 .. ln W_{n_bins-1}],
+ *   s_j = exp(clamp(net(z)_j, -log_clamp, log_clamp)),
+ * with W_m the binned window power of bps_window_power, computed here once per
+ * chain.  The mass depends on P, not on delta, so each move still leaves the
+ * conditional of delta invariant (Sec. 4.1.2: the mass changes efficiency
+ * only).  net: input width 2 n_bins, output width = number of mass bins
+ * (1..64, linear in |n| as for P); its parameters are copied (later training
+ * of `net` does not affect ctx).  feat_mean, feat_std: host float [2 n_bins].
+ * net = NULL returns ctx to the mass of its configuration.  The data of every
+ * chain must be set. */
+typedef struct bps_mlp bps_mlp;
+bps_status bps_set_mass_net(bps_ctx* ctx, const bps_mlp* net, const float* feat_mean, const float* feat_std,
+                            double log_clamp);
+
+/* The mass multipliers in use by chain `chain` (0 for a single context):
+ * *n_mass_bins receives their number, scales (host double [64]) the values. */
+bps_status bps_get_mass_scale(bps_ctx* ctx, int chain, int* n_mass_bins, double* scales);
+
 /* ---- the mass-preconditioner network ----
  * A multilayer perceptron (ReLU hidden layers, linear output) that maps binned
  * features of a problem to per-bin log multipliers of the diagonal mass (for
@@ -213,7 +239,6 @@ bps_status bps_set_mass_scale(bps_ctx* ctx, int n_mass_bins, const double* scale
  * use BF16 operands with FP32 accumulation on the tensor cores; parameters and
  * Adam moments are FP32.  Parameters are one FP32 vector, layer by layer: W_l
  * [n_l][n_{l+1}] row-major, then b_l [n_{l+1}].  Loss: mean squared error. */
-typedef struct bps_mlp bps_mlp;
 /* sizes[0..n_layers]: input, hidden..., output widths (each 1..512; 1..4 layers). */
 bps_status bps_mlp_create(int n_layers, const int* sizes, void* cuda_stream, bps_mlp** out);
 size_t bps_mlp_num_params(const bps_mlp* net);

@@ -186,6 +186,7 @@ class Chain:
         self.seed = seed
         self.iteration = iteration
         self.P_ref = self.P.copy()
+        self.mass_fn = None
         self.consts = data_constants(self.counts, self.R)
         self.rebuild()
 
@@ -194,8 +195,11 @@ class Chain:
         self.abar = float(np.mean(self.a))
 
     def hmc_step(self):
+        # mass_fn (optional): chain -> per-mode multipliers of the diagonal mass,
+        # a function of the hyperparameters only (Sec. 4.1.2 leaves the mass free)
+        scale = self.mass_fn(self) if self.mass_fn is not None else None
         self.delta_hat, info = hmc.hmc_move(self.geom, self.delta_hat, self.P, self.a, self.c, self.abar,
-                                            self.n_leapfrog, self.eps_max, self.seed, self.iteration)
+                                            self.n_leapfrog, self.eps_max, self.seed, self.iteration, scale)
         return info
 
     def sample_power(self):

@@ -82,6 +82,8 @@ _SIGS = {
     "bps_mlp_destroy": ([_P], None),
     "bps_mass_stats": ([_P, ctypes.c_int, ctypes.c_int, _D], ctypes.c_int),
     "bps_window_power": ([_P, _D], ctypes.c_int),
+    "bps_set_mass_net": ([_P, _P, _P, _P, ctypes.c_double], ctypes.c_int),
+    "bps_get_mass_scale": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D], ctypes.c_int),
     "bps_bin_power_noalloc": ([ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "bps_destroy": ([_P], None),
 }
@@ -401,6 +403,24 @@ def bps_window_power(ctx, n_bins, n_slots=1):
     out = np.zeros(n_slots * n_bins)
     _check(ctx, load().bps_window_power(ctx, out.ctypes.data_as(_D)))
     return out.reshape(n_slots, n_bins)
+
+
+def bps_set_mass_net(ctx, net, feat_mean=None, feat_std=None, log_clamp=None):
+    """Install `net` (an MLP) as the per-move mass of ctx; net=None removes it."""
+    if net is None:
+        _check(ctx, load().bps_set_mass_net(ctx, None, None, None, 1.0))
+        return
+    mu = np.ascontiguousarray(feat_mean, dtype=np.float32)
+    sd = np.ascontiguousarray(feat_std, dtype=np.float32)
+    _check(ctx, load().bps_set_mass_net(ctx, net.ptr, mu.ctypes.data_as(_P), sd.ctypes.data_as(_P),
+                                        float(log_clamp)))
+
+
+def bps_get_mass_scale(ctx, chain=0):
+    n = ctypes.c_int(0)
+    out = np.zeros(64)
+    _check(ctx, load().bps_get_mass_scale(ctx, int(chain), ctypes.byref(n), out.ctypes.data_as(_D)))
+    return out[:n.value].copy()
 
 
 def bps_version():

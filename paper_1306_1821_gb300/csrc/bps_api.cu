@@ -54,6 +54,7 @@ struct bps_ctx {
   int chain_cap = 0;
   double* host_buf = nullptr;   // pinned staging for small reads
   int n_mass = 0;
+  MassNet* mnet = nullptr;      // network mass (bps_set_mass_net): scales recomputed before every move
   std::vector<char> have_data;
   int rebuild_blocks = 0;
   int n_sm = 0;
@@ -138,7 +139,7 @@ Fields fields(bps_ctx* c) {
   f.part_stride = c->part_stride;
   f.tw = c->tw;
   f.inv_nv = (float)(1.0 / (double)c->nv);
-  f.mass_mode = c->cfg.mass_mode;
+  f.mass_mode = (c->cfg.mass_mode != 0 || c->mnet) ? 1 : 0;
   f.n_sm = c->n_sm;
   f.spec_stride = (long long)c->n_spec;
   f.real_stride = c->nv;
@@ -304,6 +305,7 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   cudaStream_t s = ctx->stream;
   const PassTable& P = ctx->pt;
   const int L = ctx->cfg.n_leapfrog, B = ctx->batch;
+  if (ctx->mnet) launch_mass_net(sa, ctx->mnet, B, s);
   launch_move_begin(sa, B, s);
   P.z_noise(f, B, s);
   P.y_fwd(f, BUF_PH, B, s);
@@ -328,7 +330,7 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   P.x_final(f, region_offset(ctx, RG_FINAL), B, s);
   launch_move_end(sa, region_offset(ctx, RG_INIT), region_offset(ctx, RG_LIK0), region_offset(ctx, RG_FINAL),
                   region_offset(ctx, RG_LIK1), P.x_tiles, P.z_tiles, B, s);
-  int n = 9 + 4 * L;
+  int n = 9 + 4 * L + (ctx->mnet ? 1 : 0);
   if (advance) {
     launch_advance(ctx->ds, B, s);
     ++n;
@@ -491,6 +493,7 @@ void free_all(bps_ctx* c) {
   cudaFree(c->part);
   cudaFree(c->ds);
   cudaFree(c->chain_dev);
+  massnet_destroy(c->mnet);
   if (c->host_buf) cudaFreeHost(c->host_buf);
 }
 
@@ -814,8 +817,11 @@ bps_status run_iterations(bps_ctx* top, const std::vector<bps_ctx*>& groups, int
 // the diagonal mass 1/lambda_k + abar over the same modes.
 bps_status mass_stats(bps_ctx* ctx, int n_moves, int n_mass, double* out, int out_stride, const std::vector<int>& slot) {
   int thr[MAXB];
-  if (!bin_tables(ctx->N, n_mass, thr, nullptr))
-    return fail(ctx, BPS_EINVAL, "a mass bin holds no |n|^2 value; use fewer mass bins");
+  double nm[MAXB];
+  if (!bin_tables(ctx->N, n_mass, thr, nm))
+    return fail(ctx, BPS_EINVAL, "a mass bin holds no mode; use fewer mass bins");
+  if (ctx->mnet && n_mass != ctx->n_mass)
+    return fail(ctx, BPS_EINVAL, "with a network mass, n_mass_bins must equal the network's output width");
   cudaStream_t s = ctx->stream;
   const int B = ctx->batch;
   if (!ctx->acc) {
@@ -1123,6 +1129,73 @@ bps_status bps_set_mass_scale(bps_ctx* ctx, int n_mass_bins, const double* scale
   }
   drop_graph(ctx);   // the number of mass bins is a launch argument
   return BPS_OK;
+}
+
+bps_status bps_set_mass_net(bps_ctx* ctx, const bps_mlp* net, const float* feat_mean, const float* feat_std,
+                            double log_clamp) {
+  if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
+  std::vector<bps_ctx*> gs = ctx->is_batch ? ctx->groups : std::vector<bps_ctx*>{ctx};
+  drop_graph(ctx);
+  if (!net) {
+    for (bps_ctx* g : gs) {
+      massnet_destroy(g->mnet);
+      g->mnet = nullptr;
+    }
+    return BPS_OK;
+  }
+  const int nb = ctx->cfg.n_bins, n_out = massnet_width(net, 1);
+  if (!feat_mean || !feat_std) return fail(ctx, BPS_EINVAL, "null argument");
+  if (massnet_width(net, 0) != 2 * nb) return fail(ctx, BPS_EINVAL, "the network must take 2 n_bins inputs");
+  if (n_out < 1 || n_out > MAXB) return fail(ctx, BPS_EINVAL, "the network must give 1..64 outputs");
+  if (!(log_clamp > 0.0) || !std::isfinite(log_clamp)) return fail(ctx, BPS_EINVAL, "log_clamp must be positive");
+  for (int i = 0; i < 2 * nb; ++i)
+    if (!(feat_std[i] > 0.f) || !std::isfinite(feat_mean[i])) return fail(ctx, BPS_EINVAL, "bad feature standardisation");
+  for (bps_ctx* g : gs) {
+    int thr[MAXB];
+    if (!bin_tables(g->N, n_out, thr, nullptr))
+      return fail(ctx, BPS_EINVAL, "a mass bin holds no |n|^2 value; use fewer network outputs");
+    for (int ch = 0; ch < g->batch; ++ch)
+      if (!g->have_data[ch]) return fail(ctx, BPS_ESTATE, "a chain has no data");
+  }
+  for (bps_ctx* g : gs) {
+    // window features of every chain: ln of the binned power of a / abar
+    std::vector<double> wp((size_t)g->batch * nb);
+    std::vector<int> slot(g->batch);
+    for (int ch = 0; ch < g->batch; ++ch) slot[ch] = ch;
+    bps_status st = window_power(g, wp.data(), nb, slot);
+    if (st != BPS_OK) return st;
+    int thr[MAXB];
+    bin_tables(g->N, n_out, thr, nullptr);
+    for (int ch = 0; ch < g->batch && st == BPS_OK; ++ch) {
+      float wf[MAXB] = {0.f};
+      for (int m = 0; m < nb; ++m) wf[m] = (float)std::log(std::max(wp[(size_t)ch * nb + m], 1e-30));
+      st = ds_write_bytes(g, ch, DS_OFF(wfeat), wf, sizeof(wf));
+      if (st == BPS_OK) st = ds_write_bytes(g, ch, DS_OFF(mthr), thr, sizeof(thr));
+    }
+    if (st != BPS_OK) return st;
+    MassNet* m = nullptr;
+    st = massnet_create(net, feat_mean, feat_std, log_clamp, &m);
+    if (st != BPS_OK) return fail(ctx, st, "network copy failed");
+    massnet_destroy(g->mnet);
+    g->mnet = m;
+    g->n_mass = n_out;
+  }
+  return BPS_OK;
+}
+
+bps_status bps_get_mass_scale(bps_ctx* ctx, int chain, int* n_mass_bins, double* scales) {
+  if (!ctx || !n_mass_bins || !scales) return fail(ctx, BPS_EINVAL, "null argument");
+  bps_ctx* g = ctx;
+  int ch = chain;
+  if (ctx->is_batch) {
+    if (chain < 0 || chain >= (int)ctx->chain_map.size()) return fail(ctx, BPS_EINVAL, "chain out of range");
+    g = ctx->groups[ctx->chain_map[chain].first];
+    ch = ctx->chain_map[chain].second;
+  } else if (chain != 0) {
+    return fail(ctx, BPS_EINVAL, "chain must be 0 for a single-chain context");
+  }
+  *n_mass_bins = g->n_mass;
+  return ds_read_bytes(g, ch, DS_OFF(mass_scale), scales, (size_t)g->n_mass * sizeof(double));
 }
 
 bps_status bps_fft_r2c(bps_ctx* ctx, const float* real_dev, float* spec_dev) {

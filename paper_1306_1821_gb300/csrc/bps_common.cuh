@@ -257,6 +257,7 @@ struct DevState {
   double lik0, lik1;
   double nmodes[MAXB];               // full-grid mode count n_m of each bin
   double mass_scale[MAXB];           // per mass-bin multipliers of the diagonal mass
+  float wfeat[MAXB];                 // ln of the window power per P bin (network mass features)
   // per-bin FP32 tables used inside the field passes
   float inv_lambda[MAXB], inv_M[MAXB], sqrt_M[MAXB];
   float inv_ms[MAXB], sqrt_ms[MAXB]; // 1/s_j and sqrt(s_j) of the mass scales

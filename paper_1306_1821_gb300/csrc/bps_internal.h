@@ -79,6 +79,16 @@ void launch_zero_dc(float2* spec, cudaStream_t s);
 
 enum JumpKind { J_FIRST = 0, J_MID = 1, J_LAST = 2 };
 
+// Device copy of the mass-preconditioner network for inference inside the
+// Gibbs iteration (bps_mlp.cu).  Before a move, launch_mass_net writes
+// DevState::mass_scale[j] = exp(clamp(net(z)_j)) per chain, with z the
+// standardised features [ln P_m, wfeat_m] of the chain's current state.
+struct MassNet;
+bps_status massnet_create(const bps_mlp* net, const float* mean, const float* sd, double log_clamp, MassNet** out);
+void massnet_destroy(MassNet* m);
+int massnet_width(const bps_mlp* net, int output);   // input width (output = 0) or output width (1)
+void launch_mass_net(const ScalarArgs& a, const MassNet* m, int nch, cudaStream_t s);
+
 // Text returned by bps_last_error(NULL) for context-free calls.
 void set_last_error(const char* msg);
 

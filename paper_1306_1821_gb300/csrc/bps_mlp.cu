@@ -19,6 +19,7 @@ namespace {
 
 constexpr int MLP_MAX_LAYERS = 4;
 constexpr int MLP_MAX_WIDTH = 512;
+constexpr float MASSNET_ZMAX = 4.0f;   // clamp of the standardised network-mass features
 
 // ------------------------------------------------------------------ GEMM
 // C[M x N] = op(A)[M x K] op(B)[K x N] (+ bias[N]) (ReLU if act), FP32 in and
@@ -144,7 +145,77 @@ __global__ void k_sum(const double* part, int n, double* out) {
   *out = s;
 }
 
+__global__ void k_to_bf16(long long n, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
 }  // namespace
+
+// ------------------------------------------------------------------ in-graph inference
+// One device allocation: this header, then per layer the BF16 weights and the
+// FP32 biases at the byte offsets below (16-byte aligned).
+struct MassNet {
+  int n_layers;
+  int sizes[MLP_MAX_LAYERS + 1];
+  long long off_w[MLP_MAX_LAYERS], off_b[MLP_MAX_LAYERS];
+  float mean[MLP_MAX_WIDTH], sd[MLP_MAX_WIDTH];
+  float log_clamp;
+};
+
+namespace {
+
+// One block per chain: the features [ln P_m, ln W_m] of the chain's current
+// state, standardised and clamped to +-MASSNET_ZMAX (a state far outside the
+// training range, e.g. a bin whose P drifts, must not drive the network to
+// arbitrary outputs), through the network with the numerics of the training
+// kernels (operands rounded to BF16, FP32 accumulation, FP32 bias and ReLU),
+// then s_j = exp(clamp(y_j)) into the chain's mass scales.  A matrix-vector
+// product per layer (at most 512 x 512): FP32 FMAs over coalesced weight rows.
+__global__ void __launch_bounds__(256) k_mass_net(ScalarArgs a, const MassNet* __restrict__ m) {
+  DevState* ds = a.ds + blockIdx.y;
+  __shared__ float h[2][MLP_MAX_WIDTH];
+  const int t = threadIdx.x, nb = a.n_bins;
+  const char* base = reinterpret_cast<const char*>(m);
+  const int n0 = m->sizes[0];
+  for (int i = t; i < n0; i += blockDim.x) {
+    const float f = i < nb ? (float)log(ds->P[i]) : ds->wfeat[i - nb];
+    const float z = (f - m->mean[i]) / m->sd[i];
+    h[0][i] = bf16_round(fminf(fmaxf(z, -MASSNET_ZMAX), MASSNET_ZMAX));
+  }
+  __syncthreads();
+  int cur = 0;
+  const int L = m->n_layers;
+  for (int l = 0; l < L; ++l) {
+    const int ni = m->sizes[l], no = m->sizes[l + 1];
+    const __nv_bfloat16* W = reinterpret_cast<const __nv_bfloat16*>(base + m->off_w[l]);
+    const float* b = reinterpret_cast<const float*>(base + m->off_b[l]);
+    for (int j = t; j < no; j += blockDim.x) {
+      float acc = 0.f;
+      for (int i = 0; i < ni; ++i) acc = fmaf(h[cur][i], __bfloat162float(W[(long long)i * no + j]), acc);
+      float v = acc + b[j];
+      if (l < L - 1) v = bf16_round(fmaxf(v, 0.f));
+      h[cur ^ 1][j] = v;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  const float c = m->log_clamp;
+  for (int j = t; j < m->sizes[L]; j += blockDim.x) ds->mass_scale[j] = exp((double)fminf(fmaxf(h[cur][j], -c), c));
+}
+
+}  // namespace
+
+int massnet_width(const bps_mlp* net, int output);
+bps_status massnet_create(const bps_mlp* net, const float* mean, const float* sd, double log_clamp, MassNet** out);
+void massnet_destroy(MassNet* m) { cudaFree(m); }
+
+void launch_mass_net(const ScalarArgs& a, const MassNet* m, int nch, cudaStream_t s) {
+  k_mass_net<<<dim3(1, nch), 256, 0, s>>>(a, m);
+}
+
 }  // namespace bps
 
 using namespace bps;
@@ -384,3 +455,50 @@ bps_status bps_mlp_train(bps_mlp* net, int n_examples, const float* x_dev, const
 }
 
 }  // extern "C"
+
+namespace bps {
+
+int massnet_width(const bps_mlp* net, int output) { return output ? net->sizes[net->L] : net->sizes[0]; }
+
+bps_status massnet_create(const bps_mlp* net, const float* mean, const float* sd, double log_clamp, MassNet** out) {
+  *out = nullptr;
+  MassNet h{};
+  h.n_layers = net->L;
+  auto up16 = [](long long x) { return (x + 15) & ~15LL; };
+  long long off = up16((long long)sizeof(MassNet));
+  for (int l = 0; l <= net->L; ++l) h.sizes[l] = net->sizes[l];
+  for (int l = 0; l < net->L; ++l) {
+    h.off_w[l] = off;
+    off = up16(off + 2LL * net->sizes[l] * net->sizes[l + 1]);
+    h.off_b[l] = off;
+    off = up16(off + 4LL * net->sizes[l + 1]);
+  }
+  for (int i = 0; i < net->sizes[0]; ++i) {
+    h.mean[i] = mean[i];
+    h.sd[i] = sd[i];
+  }
+  h.log_clamp = (float)log_clamp;
+  char* blob = nullptr;
+  if (cudaMalloc((void**)&blob, (size_t)off) != cudaSuccess) {
+    cudaGetLastError();
+    return mfail(nullptr, BPS_ENOMEM, "network copy allocation failed");
+  }
+  cudaStream_t s = net->stream;
+  bool ok = cudaMemcpyAsync(blob, &h, sizeof(MassNet), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  for (int l = 0; l < net->L && ok; ++l) {
+    const long long nw = (long long)net->sizes[l] * net->sizes[l + 1];
+    k_to_bf16<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(nw, net->p + net->off_w[l],
+                                                          reinterpret_cast<__nv_bfloat16*>(blob + h.off_w[l]));
+    ok = cudaMemcpyAsync(blob + h.off_b[l], net->p + net->off_b[l], 4 * (size_t)net->sizes[l + 1],
+                         cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+  }
+  ok = ok && cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaFree(blob);
+    return mfail(nullptr, BPS_ECUDA, "network copy failed");
+  }
+  *out = reinterpret_cast<MassNet*>(blob);
+  return BPS_OK;
+}
+
+}  // namespace bps

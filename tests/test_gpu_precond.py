@@ -120,3 +120,82 @@ def test_unit_scales_equal_the_plain_mass():
     finally:
         a.close()
         b.close()
+
+
+def oracle_net_scales(params, P, W, mu, sd, clamp):
+    """exp(clamp(net(z))) of the oracle network with BF16-rounded operands."""
+    from oracle import mlp
+    f = np.concatenate([np.log(P), np.log(W)]).astype(np.float32).astype(np.float64)
+    z = np.clip(((f - mu) / sd).astype(np.float32), -4, 4).astype(np.float64)
+    y, _ = mlp.forward(params, z[None, :], mlp.round_bf16)
+    return np.exp(np.clip(y[0], -clamp, clamp))
+
+
+def random_net(n_in, n_out, seed):
+    from oracle import mlp
+    from paper_1306_1821_gb300 import bps
+    rng = np.random.default_rng(seed)
+    sizes = [n_in, 32, 32, n_out]
+    params = mlp.init_params(sizes, seed)
+    for i in range(1, len(params), 2):
+        params[i] = rng.standard_normal(params[i].shape) * 0.1
+    params[-2] *= 0.3
+    net = bps.MLP(sizes)
+    net.set_params(bps.flatten_params(params))
+    p32 = bps.unflatten_params(net.get_params(), sizes)
+    mu = rng.standard_normal(n_in).astype(np.float32)
+    sd = rng.uniform(0.5, 2.0, n_in).astype(np.float32)
+    return net, p32, mu.astype(np.float64), sd.astype(np.float64)
+
+
+def test_network_mass_is_evaluated_on_the_device_from_the_current_state():
+    from oracle import gibbs
+    from paper_1306_1821_gb300 import bps
+    pb = Problem(16, n_sub=2, n_bins=4, n_leapfrog=6, eps_max=0.1)
+    n_mass, clamp = 5, np.log(16.0)
+    net, p32, mu, sd = random_net(8, n_mass, 3)
+    s = sampler(pb, 41, 0)
+    try:
+        bps.bps_set_mass_net(s.ctx, net, mu, sd, clamp)
+        net.close()                       # the context holds its own copy
+        a, _ = model.local_fields(pb.counts, pb.R, pb.b, pb.nbar)
+        W = gibbs.bin_power(pb.geom, grid.forward(a / a.mean()))
+        for _ in range(2):
+            bps.bps_gibbs_iterate(s.ctx, 1)
+            P, _, _, _ = bps.bps_get_state(s.ctx, None, pb.wl.n_bins, pb.wl.n_sub)
+            bps.bps_hmc_step(s.ctx)           # scales from the P after the iteration
+            got = bps.bps_get_mass_scale(s.ctx)
+            assert got.size == n_mass
+            ref = oracle_net_scales(p32, P[:4], W, mu, sd, clamp)
+            assert np.max(np.abs(np.log(got / ref))) < 5e-3, (got, ref)
+        bps.bps_set_mass_net(s.ctx, None)
+    finally:
+        s.close()
+
+
+def test_gibbs_with_network_mass_matches_oracle_chain():
+    from oracle import gibbs
+    from paper_1306_1821_gb300 import bps
+    pb = Problem(16, n_sub=2, n_bins=4, n_leapfrog=6, eps_max=0.3)
+    n_mass, clamp = 6, np.log(16.0)
+    net, p32, mu, sd = random_net(8, n_mass, 8)
+    s = sampler(pb, 43, 0)
+    try:
+        bps.bps_set_mass_net(s.ctx, net, mu, sd, clamp)
+        ch = pb.oracle_chain(seed=43)
+        a, _ = model.local_fields(pb.counts, pb.R, pb.b, pb.nbar)
+        W = gibbs.bin_power(pb.geom, grid.forward(a / a.mean()))
+        gm = grid.Geometry(16, pb.wl.box, n_mass)
+        ch.mass_fn = lambda c: gm.per_mode(oracle_net_scales(p32, c.P, W, mu, sd, clamp), dc=1.0)
+        rec = bps.bps_gibbs_iterate(s.ctx, 3, rec_len=4 + 2 * 2 + 2)
+        for i in range(3):
+            r = ch.iterate()
+            if abs(r["hmc"]["dH"] + math.log(r["hmc"]["u_acc"])) < 1e-3:
+                pytest.skip("decision within the tolerance band; states may legitimately differ")
+            assert abs(rec[i, -2] - r["hmc"]["dH"]) < 1e-3
+            assert bool(rec[i, -1]) == r["hmc"]["accepted"]
+            assert np.max(np.abs(rec[i, :4] / r["P"] - 1)) < 1e-4
+        assert rel_l2(gpu_spectrum(s), ch.delta_hat) < 2e-4
+    finally:
+        net.close()
+        s.close()
