@@ -34,6 +34,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "xleap_survey256_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1306_1821_gb300", "csrc", f)
                   for f in ("bps_passes.cu", "bps_passes.cuh", "bps_common.cuh")]
 KERNEL_NAMES = ["x pass (kick+drift+IFFT_x)", "y pass inverse", "z pass (C2R, local force, R2C)", "y pass forward"]
+PROFILE_EVERY = 10      # one event-timed iteration per this many in the timed region
 
 
 # ---------------------------------------------------------------- helpers
@@ -202,7 +203,7 @@ def config_dict(wl, where):
                         f"({wl.jump_leapfrog} steps), one Gibbs iteration per step",
             "grid": wl.N, "box_mpc_h": wl.box, "n_sub": wl.n_sub, "n_bins": wl.n_bins,
             "leapfrog_per_step": wl.n_leapfrog, "jump_leapfrog_per_step": wl.jump_leapfrog,
-            "l2": "inputs larger than L2 (each half spectrum 68 MB, 0.95 GB moved per leapfrog)",
+            "l2": "inputs larger than L2 (each half spectrum 68 MB; a, c 67 MB each)",
             "parallelism": "replicas (one chain per GPU)" if where != "cpu" else "single host thread"}
 
 
@@ -244,24 +245,34 @@ def run_ours(args):
     if args.warmup > 0:
         bps.bps_gibbs_iterate(s.ctx, args.warmup)
 
-    # ---- device-timed region: K Gibbs iterations, inputs resident in HBM
-    bps.bps_profile(s.ctx, 1)
+    # ---- device-timed region: K Gibbs iterations, inputs resident in HBM.  Every
+    # PROFILE_EVERY-th iteration runs with per-stage event pairs (launched
+    # directly); the others replay the iteration's CUDA graph.
     bps.bps_profile_read(s.ctx)
     l0 = bps.bps_kernel_launches(s.ctx)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    recs = []
     with ClockSampler(dev.index) as clk:
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize(dev)
         e0.record(stream)
-        rec = bps.bps_gibbs_iterate(s.ctx, args.steps, s.rec_len)
+        done = 0
+        while done < args.steps:
+            n = min(PROFILE_EVERY, args.steps - done)
+            bps.bps_profile(s.ctx, 1)
+            recs.append(bps.bps_gibbs_iterate(s.ctx, 1, s.rec_len))
+            bps.bps_profile(s.ctx, 0)
+            if n > 1:
+                recs.append(bps.bps_gibbs_iterate(s.ctx, n - 1, s.rec_len))
+            done += n
         e1.record(stream)
         torch.cuda.synchronize(dev)
+    rec = np.concatenate(recs, 0)
     launches = bps.bps_kernel_launches(s.ctx) - l0
     kms, kn = bps.bps_profile_read(s.ctx)
-    bps.bps_profile(s.ctx, 0)
     local_s = e0.elapsed_time(e1) / 1000.0
     secs, units = aggregate(local_s, args.steps * wl.n_leapfrog, ws, dev)
     if ws > 1:
@@ -284,6 +295,20 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     e2e_secs, e2e_units = aggregate(e2e_s, k_e2e * wl.n_leapfrog, ws, dev)
+
+    # ---- P(k) effective samples per second of this (plain diagonal mass) chain:
+    # ESS of ln P_m over a further run of Gibbs iterations, timed with events
+    pk = None
+    if args.ess_iters > 0:
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        f0.record(stream)
+        rec_e = bps.bps_gibbs_iterate(s.ctx, args.ess_iters, s.rec_len)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        pk = pk_ess(rec_e, wl.n_bins, wl.N, f0.elapsed_time(f1) / 1000.0)
+        pk["mass"] = "plain diagonal Fourier mass (Eq. Mass_matrix)"
 
     # ---- roofline of the dominant kernel (the x pass), from the live events
     S_c = wl.N * wl.N * (wl.N // 2 + 1) * 8
@@ -320,10 +345,12 @@ def run_ours(args):
                          "kernel": KERNEL_NAMES[dom], "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": bytes_kind[dom], "launch_ms": per_launch_ms[dom]},
-            "leapfrog_kernels": {KERNEL_NAMES[i]: {"ms": per_launch_ms[i], "launches": int(kn[i]),
-                                                   "share": shares[i],
+            "leapfrog_kernels": {KERNEL_NAMES[i]: {"ms": per_launch_ms[i], "timed_launches": int(kn[i]),
+                                                   "share": shares[i], "bytes": bytes_kind[i],
                                                    "GBps": bytes_kind[i] / (per_launch_ms[i] * 1e-3) / 1e9}
                                  for i in range(4)},
+            "profiled_iterations": f"1 in {PROFILE_EVERY} (event pairs around each leapfrog kernel, launched "
+                                   f"directly); the rest replay the iteration's CUDA graph",
             "leapfrog_roofline": {"bytes": leap_bytes, "ms": leap_ms,
                                   "GBps": leap_bytes / (leap_ms * 1e-3) / 1e9,
                                   "frac": leap_bytes / (leap_ms * 1e-3) / 1e9 / peak},
@@ -333,6 +360,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
+        if pk is not None:
+            line["pk_ess"] = pk
         if ws == 1 and not args.no_cpu_baseline:
             v, dt = oracle_leapfrog_rate(wl, counts, R, n_steps=2)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -518,8 +547,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96", "precond128"])
-    ap.add_argument("--ess-iters", type=int, default=20000,
-                    help="Gibbs iterations per arm of --workload precond128")
+    ap.add_argument("--ess-iters", type=int, default=None,
+                    help="Gibbs iterations of the P(k) ESS run (default 2000 at 256^3, 20000 per arm of precond128; "
+                         "0 skips it)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -528,7 +558,11 @@ def main(argv=None):
     if args.workload == "batch96":
         return run_batch(args)
     if args.workload == "precond128":
+        if args.ess_iters is None:
+            args.ess_iters = 20000
         return run_precond(args)
+    if args.ess_iters is None:
+        args.ess_iters = 2000
     return run_ours(args)
 
 

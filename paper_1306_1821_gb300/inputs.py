@@ -64,7 +64,7 @@ WORKLOADS = {
                           n_leapfrog=10, eps_max=0.06),
     # 256^3, L = 1000 Mpc/h, six subsamples, 32 bins, 20 leapfrog steps, jump on
     "survey256": Workload("survey256", 256, 1000.0, 32, SIX_B, _six_nbar(), 0.25, "gauss",
-                          n_leapfrog=20, eps_max=0.05, jump=True, jump_leapfrog=10),
+                          n_leapfrog=20, eps_max=0.05, jump=True, jump_leapfrog=10, jump_eps_max=0.15),
 }
 
 
