@@ -140,6 +140,8 @@ Fields fields(bps_ctx* c) {
   f.tw = c->tw;
   f.inv_nv = (float)(1.0 / (double)c->nv);
   f.mass_mode = (c->cfg.mass_mode != 0 || c->mnet) ? 1 : 0;
+  f.n_bins = c->cfg.n_bins;
+  f.n_mass = c->n_mass;
   f.n_sm = c->n_sm;
   f.spec_stride = (long long)c->n_spec;
   f.real_stride = c->nv;

@@ -164,6 +164,10 @@ template <> struct Grid<96>  { static constexpr int R1 = 12, R2 = 8;  };
 template <> struct Grid<128> { static constexpr int R1 = 16, R2 = 8;  };
 template <> struct Grid<256> { static constexpr int R1 = 16, R2 = 16; };
 
+#ifndef BPS_ZPAIRS
+#define BPS_ZPAIRS 8
+#endif
+
 template <int N>
 struct Cfg {
   static constexpr int R1 = Grid<N>::R1;
@@ -173,11 +177,11 @@ struct Cfg {
   static constexpr int ZP = ((H + 1) + 1) / 2 * 2;     // padded row length (complex)
   static constexpr int F = H < 16 ? H : 16;            // tile columns
   static constexpr int NT = F * RMAX < 32 ? 32 : F * RMAX;  // threads per strided tile
-  static constexpr int NTZ = 16 * RMAX;                // threads per contiguous-axis tile
+  static constexpr int LP = BPS_ZPAIRS;                // line pairs per contiguous-axis tile
+  static constexpr int NTZ = LP * RMAX;                // threads per contiguous-axis tile
   static constexpr int ZB = H / F;                     // regular column blocks per row
   static constexpr int NYQ = N / F;                    // Nyquist tiles per pass
   static constexpr int TILES = N * ZB + NYQ;           // tiles of one strided pass
-  static constexpr int LP = 16;                        // line pairs per contiguous-axis tile
   static constexpr int ZTILES = N * N / (2 * LP);
   static_assert(R1 * R2 == N, "bad split");
   static_assert(H % F == 0, "bad tile");

@@ -107,18 +107,19 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
   const long long colo = T.base + (long long)f * T.cs;
   const int cur = ds->cur;
   const bool mm = fp.mass_mode != 0;
+  const float scb = bin_scale(fp.n_bins, N), scm = bin_scale(fp.n_mass, N);
 
   float2 v[C::RMAX];
   auto mode_bin = [&](int k, float& il, float& im, float& sm) -> int {
     const int nx = sgn_n<N>(k);
     const int n2 = nx * nx + n2yz;
-    const int m = bin_of(n2, s_thr);
+    const int m = bin_est(n2, s_thr, scb, fp.n_bins);
     if (m >= 0) {
       il = s_il[m];
       im = s_im[m];
       sm = s_sm[m];
       if (mm) {
-        const int j = bin_of(n2, s_mthr);
+        const int j = bin_est(n2, s_mthr, scm, fp.n_mass);
         im *= s_ims[j];
         sm *= s_sms[j];
       }
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
         for (int d = 0; d < R1; ++d) {
           const int k = jc + R2 * d;
           const int nx = sgn_n<N>(k);
-          const int m = bin_of(nx * nx + n2yz, s_thr);
+          const int m = bin_est(nx * nx + n2yz, s_thr, scb, fp.n_bins);
           v[d] = m >= 0 ? cscale(v[d], s_js[m]) : make_float2(0.f, 0.f);
         }
       }
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
       for (int d = 0; d < R1; ++d) {
         const int k = jc + R2 * d;
         const int nx = sgn_n<N>(k);
-        const int m = bin_of(nx * nx + n2yz, s_thr);
+        const int m = bin_est(nx * nx + n2yz, s_thr, scb, fp.n_bins);
         const long long idx = colo + (long long)k * T.rs;
         dsel(fp, cur)[idx] = m >= 0 ? cscale(dsel(fp, cur)[idx], s_js[m]) : make_float2(0.f, 0.f);
       }
@@ -331,6 +332,17 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
 
   if constexpr (BINNED) {
     const int warp = t >> 5;
+    // all loads of the column first (one round trip), then the warp-level bin sums
+    float ev[R1];
+    int mv[R1];
+    float2 xv[R1];
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < R1; ++d) {
+        const long long idx = colo + (long long)(jc + R2 * d) * T.rs;
+        xv[d] = (MODE == X_MMEAN) ? fp.acc[idx] : (MODE == X_WPOW) ? fp.W[idx] : dsel(fp, cur)[idx];
+      }
+    }
 #pragma unroll
     for (int d = 0; d < R1; ++d) {
       float e = 0.f;
@@ -338,10 +350,10 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
       if (act) {
         const int k = jc + R2 * d;
         const int nx = sgn_n<N>(k);
-        m = bin_of(nx * nx + n2yz, MASSBINS ? s_mthr : s_thr);
-        const long long idx = colo + (long long)k * T.rs;
-        float2 x = (MODE == X_MMEAN) ? fp.acc[idx] : (MODE == X_WPOW) ? fp.W[idx] : dsel(fp, cur)[idx];
+        m = MASSBINS ? bin_est(nx * nx + n2yz, s_mthr, scm, fp.n_mass) : bin_est(nx * nx + n2yz, s_thr, scb, fp.n_bins);
+        const float2 x = xv[d];
         if constexpr (MODE == X_MACC) {
+          const long long idx = colo + (long long)k * T.rs;
           const float2 s0 = fp.acc[idx];
           fp.acc[idx] = make_float2(s0.x + x.x, s0.y + x.y);
         }
@@ -354,8 +366,11 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
           }
         }
       }
-      bin_accumulate<F>(e, m, s_wb[warp]);
+      ev[d] = e;
+      mv[d] = m;
     }
+#pragma unroll
+    for (int d = 0; d < R1; ++d) bin_accumulate<F>(ev[d], mv[d], s_wb[warp]);
     __syncthreads();
     for (int m = t; m < MAXB; m += NT) {
       double s = 0.0;
@@ -410,14 +425,14 @@ __global__ void __launch_bounds__(Cfg<N>::NT) k_ypass(Fields fp0, int buf) {
 }
 
 // ------------------------------------------------------------------ z pass
-// 16 pairs of consecutive z lines per tile; line 2f is the real part and line
+// LP pairs of consecutive z lines per tile; line 2f is the real part and line
 // 2f+1 the imaginary part of one complex transform of length N.  The lines of
 // the tile are contiguous in HBM and arrive by bulk copies.
 template <int N, int MODE>
 struct ZSmem {
   using C = Cfg<N>;
   static constexpr int LINES = 2 * C::LP;
-  static constexpr size_t BUF = (size_t)16 * (N + C::RMAX) * sizeof(float2);
+  static constexpr size_t BUF = (size_t)C::LP * (N + C::RMAX) * sizeof(float2);
   static constexpr size_t AC = MODE == Z_GRAD ? (size_t)LINES * N * sizeof(float) : 0;
   static constexpr size_t OFF_BUF = 0;
   static constexpr size_t OFF_A = BUF;
@@ -487,7 +502,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
   if constexpr (MODE == Z_GRAD || MODE == Z_C2R || MODE == Z_SUMS) {
     {
       const int f = t / R2, a = t % R2;
-      if (f < 16) {
+      if (f < C::LP) {
 #pragma unroll
         for (int b = 0; b < R1; ++b) {
           const int k = a + R2 * b;
@@ -505,7 +520,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
       }
     }
     __syncthreads();
-    fft2<N, R2, R1, INV, MAP_ROW, 16>(v, s_buf, s_tw, t);
+    fft2<N, R2, R1, INV, MAP_ROW, C::LP>(v, s_buf, s_tw, t);
   } else {
     float* sr = reinterpret_cast<float*>(s_buf);
     if constexpr (MODE == Z_NOISE) {
@@ -528,7 +543,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
       __syncthreads();
     }
     const int f = t / R1, c = t % R1;
-    if (f < 16) {
+    if (f < C::LP) {
 #pragma unroll
       for (int d = 0; d < R2; ++d) {
         const int n = c + R1 * d;
@@ -538,12 +553,12 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
     __syncthreads();
   }
 
-  // here: thread (f = t / R1, c = t % R1), f < 16, holds y[c + R1 d], d < R2
+  // here: thread (f = t / R1, c = t % R1), f < LP, holds y[c + R1 d], d < R2
   if constexpr (MODE == Z_GRAD || MODE == Z_C2R || MODE == Z_SUMS) {
     const int f = t / R1, c = t % R1;
     const long long la = (L0 + 2 * f) * N, lb = la + N;
     if constexpr (MODE == Z_C2R) {
-      if (f < 16) {
+      if (f < C::LP) {
 #pragma unroll
         for (int d = 0; d < R2; ++d) {
           const int n = c + R1 * d;
@@ -558,7 +573,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
       const int nsub = ds->nsub;
       for (int l = 0; l < nsub; ++l) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        if (f < 16) {
+        if (f < C::LP) {
           const uint16_t* cn = fp.cnt + l * nv;
           const float* rr = fp.R + l * nv;
 #pragma unroll
@@ -585,7 +600,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
     // Z_GRAD: the local force g = a delta - c (Eq. Wiener_Posterior_force) and the
     // likelihood energy (1/2) sum (a delta^2 - 2 c delta)
     float e = 0.f;
-    if (f < 16) {
+    if (f < C::LP) {
       const int ra = (2 * f) * N, rb = ra + N;
 #pragma unroll
       for (int d = 0; d < R2; ++d) {
@@ -604,10 +619,10 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
   }
 
   // forward transform of the packed pair, then split into the two half spectra
-  fft2<N, R1, R2, FWD, MAP_ROW, 16>(v, s_buf, s_tw, t);
+  fft2<N, R1, R2, FWD, MAP_ROW, C::LP>(v, s_buf, s_tw, t);
   {
     const int f = t / R2, c = t % R2;
-    if (f < 16) {
+    if (f < C::LP) {
 #pragma unroll
       for (int d = 0; d < R1; ++d) s_buf[f * N + c + R2 * d] = v[d];
     }

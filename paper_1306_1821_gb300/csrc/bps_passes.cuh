@@ -36,6 +36,7 @@ struct Fields {
   const float2* tw;       // W_N^j = exp(-2 pi i j / N), j < N (FP64-rounded)
   float inv_nv;           // 1 / N^3
   int mass_mode;
+  int n_bins, n_mass;     // entries of the P-bin and mass-bin threshold tables
   int n_sm;               // streaming multiprocessors
   // chains of one batch: chain j's buffers sit at j times these strides
   long long spec_stride;  // complex elements per half spectrum
@@ -154,6 +155,21 @@ __device__ __forceinline__ int bin_of(int n2, const int* thr) {
   for (int s = 32; s > 0; s >>= 1)
     if (thr[lo + s] <= n2) lo += s;
   return lo;
+}
+
+// The same bin from an FP32 estimate floor(sqrt(n2) * nb / (sqrt(3) N / 2)),
+// which is never more than one bin off for N <= 512 and nb <= 64 (checked
+// exhaustively on the host by the test suite), corrected against the exact
+// integer thresholds: two independent table reads instead of six dependent ones.
+__device__ __forceinline__ float bin_scale(int nb, int N) { return (float)nb / (0.8660254f * (float)N); }
+__device__ __forceinline__ int bin_est(int n2, const int* thr, float scale, int nb) {
+  if (n2 == 0) return -1;
+  int m = min(nb - 1, (int)(sqrtf((float)n2) * scale));
+  const int lo = thr[m];
+  const int hi = m + 1 < nb ? thr[m + 1] : 0x7fffffff;
+  if (n2 >= hi) ++m;
+  else if (n2 < lo) --m;
+  return m;
 }
 
 // ------------------------------------------------------------ reductions
