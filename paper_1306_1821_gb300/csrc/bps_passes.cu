@@ -60,6 +60,9 @@ __device__ __forceinline__ const float2* buf_ptr(const Fields& fp, int b) {
 #ifndef BPS_XPASS_MIN_BLOCKS
 #define BPS_XPASS_MIN_BLOCKS 2
 #endif
+#ifndef BPS_YPASS_MIN_BLOCKS
+#define BPS_YPASS_MIN_BLOCKS 1
+#endif
 
 // ------------------------------------------------------------------ x pass
 template <int N, int MODE>
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
 
 // ------------------------------------------------------------------ y pass
 template <int N, int DIR>
-__global__ void __launch_bounds__(Cfg<N>::NT) k_ypass(Fields fp0, int buf) {
+__global__ void __launch_bounds__(Cfg<N>::NT, BPS_YPASS_MIN_BLOCKS) k_ypass(Fields fp0, int buf) {
   const Fields fp = at_chain(fp0, blockIdx.y);
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT;

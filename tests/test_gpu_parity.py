@@ -79,7 +79,7 @@ def test_fft_roundtrip_against_numpy(torch_cuda, N):
         bps.bps_destroy(ctx)
 
 
-@pytest.mark.parametrize("N,n_sub", [(16, 1), (32, 2), (64, 3), (96, 2), (128, 2)])
+@pytest.mark.parametrize("N,n_sub", [(16, 1), (32, 2), (64, 3), (96, 2), (128, 2), (256, 1)])
 def test_gradient_and_energies(torch_cuda, N, n_sub):
     from paper_1306_1821_gb300 import bps
     torch = torch_cuda
