@@ -62,6 +62,12 @@ struct bps_ctx {
   // CUDA graph of one Gibbs iteration (captured on first use)
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
+  // host upload of survey data (bps_set_data_host): two device staging slots of
+  // one subsample's counts and response, filled on a copy stream while the
+  // data kernel of the previous subsample runs (allocated on first use)
+  char* stage = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_copied[2] = {nullptr, nullptr}, stage_free[2] = {nullptr, nullptr};
   bool graph_jump = false;
   uint64_t graph_launches = 0;   // kernels in one replay of the graph
   // leapfrog kernel timing (bps_profile)
@@ -475,6 +481,15 @@ void drop_graph(bps_ctx* c) {
 void free_streams(bps_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_stream = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (c->stage_copied[i]) cudaEventDestroy(c->stage_copied[i]);
+    if (c->stage_free[i]) cudaEventDestroy(c->stage_free[i]);
+    c->stage_copied[i] = c->stage_free[i] = nullptr;
+  }
+  cudaFree(c->stage);
+  c->stage = nullptr;
 }
 
 void free_all(bps_ctx* c) {
@@ -636,42 +651,59 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const int32_t* counts, const flo
   Fields f = fields_at(ctx, ch);
   uint16_t* cnt_ch = const_cast<uint16_t*>(f.cnt);
   float* R_ch = const_cast<float*>(f.R);
-  int32_t* ctmp = nullptr;
-  float* rtmp = nullptr;
-  if (host) {
-    // stage through this chain's spectrum work buffers (each at least N^3 * 8 bytes)
-    ctmp = reinterpret_cast<int32_t*>(f.ph);
-    rtmp = reinterpret_cast<float*>(f.W);
+  const size_t slot_bytes = (size_t)ctx->nv * (sizeof(int32_t) + sizeof(float));
+  if (host && !ctx->stage) {
+    bool ok = cudaMalloc((void**)&ctx->stage, 2 * slot_bytes) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i)
+      ok = cudaEventCreateWithFlags(&ctx->stage_copied[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ctx->stage_free[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      free_streams(ctx);
+      return fail(ctx, BPS_ENOMEM, "staging buffers for the host upload could not be allocated");
+    }
   }
   const int blocks = ctx->rebuild_blocks;
+  // per-subsample partial sums side by side (4 quantities x blocks each), read back once
   double* part = ctx->part + ch * ctx->part_cstride;
-  std::vector<double> hp(4 * (size_t)blocks);
-  std::vector<double> sR(ns), sB(ns), no(ns);
-  double bad = 0.0;
+  if ((long long)ns * 4 * blocks > ctx->part_cstride) return fail(ctx, BPS_EINVAL, "too many subsamples");
+  if (host) CK(cudaEventRecord(ctx->stage_free[0], s));   // orders the copies after earlier work on s
+  if (host) CK(cudaEventRecord(ctx->stage_free[1], s));
   for (int l = 0; l < ns; ++l) {
     const int32_t* cl = counts + (size_t)l * ctx->nv;
     const float* rl = R + (size_t)l * ctx->nv;
     if (host) {
-      CK(cudaMemcpyAsync(ctmp, cl, ctx->nv * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(rtmp, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, s));
+      // copy subsample l into slot l % 2 once the data kernel of subsample l - 2 has read it
+      const int sl = l & 1;
+      int32_t* ctmp = reinterpret_cast<int32_t*>(ctx->stage + sl * slot_bytes);
+      float* rtmp = reinterpret_cast<float*>(ctx->stage + sl * slot_bytes + (size_t)ctx->nv * sizeof(int32_t));
+      CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->stage_free[sl], 0));
+      CK(cudaMemcpyAsync(ctmp, cl, ctx->nv * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->copy_stream));
+      CK(cudaMemcpyAsync(rtmp, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_stream));
+      CK(cudaEventRecord(ctx->stage_copied[sl], ctx->copy_stream));
+      CK(cudaStreamWaitEvent(s, ctx->stage_copied[sl], 0));
       cl = ctmp;
       rl = rtmp;
     }
-    launch_data(cl, rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv, ctx->nv, part, blocks, blocks, s);
+    launch_data(cl, rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv, ctx->nv,
+                part + (size_t)l * 4 * blocks, blocks, blocks, s);
     LAUNCHED(ctx, 1);
-    CK(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    if (host) CK(cudaEventRecord(ctx->stage_free[l & 1], s));
+  }
+  std::vector<double> hp((size_t)ns * 4 * blocks);
+  CK(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> sR(ns), sB(ns), no(ns);
+  double bad = 0.0;
+  for (int l = 0; l < ns; ++l) {
     double v[4] = {0, 0, 0, 0};
     for (int q = 0; q < 4; ++q)
-      for (int b = 0; b < blocks; ++b) v[q] += hp[(size_t)q * blocks + b];
+      for (int b = 0; b < blocks; ++b) v[q] += hp[((size_t)l * 4 + q) * blocks + b];
     sR[l] = v[0];
     sB[l] = v[1];
     no[l] = v[2];
     bad += v[3];
-  }
-  if (host) {
-    CK(cudaMemsetAsync(f.ph, 0, ctx->n_spec * sizeof(float2), s));
-    CK(cudaMemsetAsync(f.W, 0, ctx->n_spec * sizeof(float2), s));
   }
   if (bad > 0.0) {
     ctx->have_data[ch] = 0;

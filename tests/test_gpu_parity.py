@@ -251,3 +251,27 @@ def test_invalid_inputs_are_rejected(torch_cuda):
             bps.bps_set_state(s.ctx, None, [-1.0, 1.0], [1.0], [1.0])
     finally:
         s.close()
+
+
+def test_host_upload_equals_device_upload(torch_cuda):
+    # the host path stages subsamples through two device slots on a copy stream
+    from paper_1306_1821_gb300 import bps
+    torch = torch_cuda
+    pb = Problem(32, n_sub=3, n_bins=4, n_leapfrog=4, eps_max=0.2)
+    a = pb.gpu(seed=13, jump=1)
+    b = pb.gpu(seed=13, jump=1)
+    try:
+        bps.bps_set_data_host(b.ctx, np.ascontiguousarray(pb.counts), np.ascontiguousarray(pb.R))
+        pinned_c = torch.from_numpy(pb.counts).pin_memory().numpy()
+        pinned_r = torch.from_numpy(pb.R).pin_memory().numpy()
+        bps.bps_set_data_host(b.ctx, pinned_c, pinned_r)        # twice: the slots are reused
+        ra = bps.bps_gibbs_iterate(a.ctx, 2, a.rec_len)
+        rb = bps.bps_gibbs_iterate(b.ctx, 2, b.rec_len)
+        assert np.array_equal(ra, rb)
+        bad = pb.counts.copy()
+        bad[2, 0, 0, 0] = -1
+        with pytest.raises(bps.BpsError):
+            bps.bps_set_data_host(b.ctx, bad, pb.R)
+    finally:
+        a.close()
+        b.close()

@@ -77,6 +77,7 @@ def test_network_mass_raises_the_effective_sample_size(trained):
     pc, _, _ = trained
     m0, s0, e0 = chain_stats(None, 0.15, 5)
     m1, s1, e1 = chain_stats(pc, 0.15, 5)
+    print("ESS plain", np.round(e0).tolist(), "network", np.round(e1).tolist())
     assert e1.min() > 2.0 * e0.min(), (e0, e1)
     assert np.all(e1[:2] > 3.0 * e0[:2]), (e0, e1)
     se = np.sqrt(s0 ** 2 / e0 + s1 ** 2 / e1)
