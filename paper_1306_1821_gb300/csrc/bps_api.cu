@@ -66,8 +66,9 @@ struct bps_ctx {
   // one subsample's counts and response, filled on a copy stream while the
   // data kernel of the previous subsample runs (allocated on first use)
   char* stage = nullptr;
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t stage_copied[2] = {nullptr, nullptr}, stage_free[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};   // counts, response: two copies in flight
+  cudaEvent_t stage_copied[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaEvent_t stage_free[2] = {nullptr, nullptr};
   bool graph_jump = false;
   uint64_t graph_launches = 0;   // kernels in one replay of the graph
   // leapfrog kernel timing (bps_profile)
@@ -481,12 +482,15 @@ void drop_graph(bps_ctx* c) {
 void free_streams(bps_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
-  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-  c->copy_stream = nullptr;
   for (int i = 0; i < 2; ++i) {
-    if (c->stage_copied[i]) cudaEventDestroy(c->stage_copied[i]);
+    if (c->copy_stream[i]) cudaStreamDestroy(c->copy_stream[i]);
+    c->copy_stream[i] = nullptr;
+    for (int k = 0; k < 2; ++k) {
+      if (c->stage_copied[i][k]) cudaEventDestroy(c->stage_copied[i][k]);
+      c->stage_copied[i][k] = nullptr;
+    }
     if (c->stage_free[i]) cudaEventDestroy(c->stage_free[i]);
-    c->stage_copied[i] = c->stage_free[i] = nullptr;
+    c->stage_free[i] = nullptr;
   }
   cudaFree(c->stage);
   c->stage = nullptr;
@@ -653,10 +657,11 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const int32_t* counts, const flo
   float* R_ch = const_cast<float*>(f.R);
   const size_t slot_bytes = (size_t)ctx->nv * (sizeof(int32_t) + sizeof(float));
   if (host && !ctx->stage) {
-    bool ok = cudaMalloc((void**)&ctx->stage, 2 * slot_bytes) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    bool ok = cudaMalloc((void**)&ctx->stage, 2 * slot_bytes) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i)
-      ok = cudaEventCreateWithFlags(&ctx->stage_copied[i], cudaEventDisableTiming) == cudaSuccess &&
+      ok = cudaStreamCreateWithFlags(&ctx->copy_stream[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ctx->stage_copied[i][0], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ctx->stage_copied[i][1], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&ctx->stage_free[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -678,11 +683,13 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const int32_t* counts, const flo
       const int sl = l & 1;
       int32_t* ctmp = reinterpret_cast<int32_t*>(ctx->stage + sl * slot_bytes);
       float* rtmp = reinterpret_cast<float*>(ctx->stage + sl * slot_bytes + (size_t)ctx->nv * sizeof(int32_t));
-      CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->stage_free[sl], 0));
-      CK(cudaMemcpyAsync(ctmp, cl, ctx->nv * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->copy_stream));
-      CK(cudaMemcpyAsync(rtmp, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_stream));
-      CK(cudaEventRecord(ctx->stage_copied[sl], ctx->copy_stream));
-      CK(cudaStreamWaitEvent(s, ctx->stage_copied[sl], 0));
+      for (int k = 0; k < 2; ++k) CK(cudaStreamWaitEvent(ctx->copy_stream[k], ctx->stage_free[sl], 0));
+      CK(cudaMemcpyAsync(ctmp, cl, ctx->nv * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->copy_stream[0]));
+      CK(cudaMemcpyAsync(rtmp, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_stream[1]));
+      for (int k = 0; k < 2; ++k) {
+        CK(cudaEventRecord(ctx->stage_copied[sl][k], ctx->copy_stream[k]));
+        CK(cudaStreamWaitEvent(s, ctx->stage_copied[sl][k], 0));
+      }
       cl = ctmp;
       rl = rtmp;
     }
