@@ -334,52 +334,116 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
   }
 
   if constexpr (BINNED) {
-    const int warp = t >> 5;
-    // all loads of the column first (one round trip), then the warp-level bin sums
-    float ev[R1];
-    int mv[R1];
-    float2 xv[R1];
+    const int warp = t >> 5, lane = t & 31;
+    // (1) every element's term into shared memory by (row kx, column f); the
+    // bin factor s_m of the jump gradient is applied per bin at the end
+    // column-major with a row stride of N + 2 floats: the writes (16 columns x 2
+    // rows per warp) and the reads (32 lanes L rows apart) both avoid bank conflicts
+    constexpr int SE = N + 2;
+    float* s_e = reinterpret_cast<float*>(s_ex);   // F * SE floats, free after the transform
     if (act) {
+      float2 xv[R1];
 #pragma unroll
       for (int d = 0; d < R1; ++d) {
         const long long idx = colo + (long long)(jc + R2 * d) * T.rs;
         xv[d] = (MODE == X_MMEAN) ? fp.acc[idx] : (MODE == X_WPOW) ? fp.W[idx] : dsel(fp, cur)[idx];
       }
-    }
 #pragma unroll
-    for (int d = 0; d < R1; ++d) {
-      float e = 0.f;
-      int m = -1;
-      if (act) {
+      for (int d = 0; d < R1; ++d) {
         const int k = jc + R2 * d;
-        const int nx = sgn_n<N>(k);
-        m = MASSBINS ? bin_est(nx * nx + n2yz, s_mthr, scm, fp.n_mass) : bin_est(nx * nx + n2yz, s_thr, scb, fp.n_bins);
         const float2 x = xv[d];
         if constexpr (MODE == X_MACC) {
           const long long idx = colo + (long long)k * T.rs;
           const float2 s0 = fp.acc[idx];
           fp.acc[idx] = make_float2(s0.x + x.x, s0.y + x.y);
         }
-        if (m >= 0) {
-          if constexpr (MODE == X_BINPOW || MODE == X_MACC || MODE == X_MMEAN || MODE == X_WPOW) {
-            e = wk * (x.x * x.x + x.y * x.y);
-          } else {
-            const float s = s_js[m];
-            e = wk * s * (v[d].x * x.x + v[d].y * x.y);
+        float e;
+        if constexpr (MODE == X_JGRAD) e = wk * (v[d].x * x.x + v[d].y * x.y);
+        else e = wk * (x.x * x.x + x.y * x.y);
+        s_e[f * SE + k] = e;
+      }
+    }
+    __syncthreads();
+    // (2) one warp per column.  Lane q takes |nx| in [q L, q L + L) (both rows
+    // kx = |nx| and N - |nx|), in rising order, so its bins rise; consecutive
+    // lanes follow each other.  A lane sums its elements into runs of equal
+    // bin: a run that starts and ends inside the lane holds a bin no other lane
+    // has and goes straight to the warp's bins; the lane's first and last runs
+    // are combined across the warp by segmented sums (the first runs and the
+    // last runs each form a bin-ordered sequence over the lanes).  Fixed order
+    // throughout: the sums are deterministic.
+    constexpr int HN = N / 2, L = (HN + 1 + 31) / 32;
+    const int* thr = MASSBINS ? s_mthr : s_thr;
+    const int nb = MASSBINS ? fp.n_mass : fp.n_bins;
+    const float scl = MASSBINS ? scm : scb;
+    double* wb = s_wb[warp];
+    for (int col = warp; col < F; col += NW) {
+      const int nyc = sgn_n<N>(T.ky0 + col * T.dky), kzc = T.kz0 + col * T.dkz;
+      const int n2c = nyc * nyc + kzc * kzc;
+      const int a0 = lane * L, a1 = min(a0 + L, HN + 1);
+      int mf = -1, ml = -1, mc = -1, nxt = 0x7fffffff;
+      float vf = 0.f, vl = 0.f, vc = 0.f;   // FP32 within the warp (FP64 is slow here); FP64 from the warp's bins on
+      bool first_done = false;
+      for (int a = a0; a < a1; ++a) {
+        const int n2 = a * a + n2c;
+        if (n2 == 0) continue;                            // the DC mode is in no bin
+        float val = s_e[col * SE + a];
+        if (a != 0 && a != HN) val += s_e[col * SE + N - a];
+        int m;
+        if (mc < 0) {
+          m = bin_est(n2, thr, scl, nb);
+          nxt = m + 1 < nb ? thr[m + 1] : 0x7fffffff;
+        } else {
+          m = mc;
+          while (n2 >= nxt) {
+            ++m;
+            nxt = m + 1 < nb ? thr[m + 1] : 0x7fffffff;
           }
         }
+        if (m != mc) {
+          if (mc >= 0) {                                  // close the current run
+            if (!first_done) { mf = mc; vf = vc; first_done = true; }
+            else wb[mc] += (double)vc;                    // a run inside this lane only
+          }
+          mc = m;
+          vc = 0.f;
+        }
+        vc += val;
       }
-      ev[d] = e;
-      mv[d] = m;
-    }
+      if (mc >= 0) {
+        if (!first_done) { mf = mc; vf = vc; ml = mc; vl = 0.f; }
+        else { ml = mc; vl = vc; }
+      }
+      // lanes without elements (beyond |nx| = N/2) carry the bin of their left
+      // neighbours with nothing, which keeps both sequences bin-ordered
+      __syncwarp();
 #pragma unroll
-    for (int d = 0; d < R1; ++d) bin_accumulate<F>(ev[d], mv[d], s_wb[warp]);
+      for (int pass = 0; pass < 2; ++pass) {
+        float vv = pass == 0 ? vf : vl;
+        int mm2 = pass == 0 ? mf : ml;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int pm = __shfl_up_sync(0xffffffffu, mm2, o);
+          if (mm2 < 0 && lane >= o) mm2 = pm;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float pv = __shfl_down_sync(0xffffffffu, vv, o);
+          const int pm = __shfl_down_sync(0xffffffffu, mm2, o);
+          if (lane + o < 32 && pm == mm2) vv += pv;
+        }
+        const int prev = __shfl_up_sync(0xffffffffu, mm2, 1);
+        if ((lane == 0 || prev != mm2) && mm2 >= 0) wb[mm2] += (double)vv;
+        __syncwarp();
+      }
+    }
     __syncthreads();
     for (int m = t; m < MAXB; m += NT) {
-      double s = 0.0;
+      double sum = 0.0;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s += s_wb[w][m];
-      fp.part[xa.region + m * fp.part_stride + blockIdx.x] = s;
+      for (int w = 0; w < NW; ++w) sum += s_wb[w][m];
+      if constexpr (MODE == X_JGRAD) sum *= (double)s_js[m];
+      fp.part[xa.region + m * fp.part_stride + blockIdx.x] = sum;
     }
     return;
   }
