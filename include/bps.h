@@ -99,8 +99,14 @@ bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* c
  * voxel has R = 0 and a count > 0, or a subsample has no observed voxel. */
 bps_status bps_set_data(bps_ctx* ctx, const int32_t* counts_dev, const float* R_dev);
 
-/* Same as bps_set_data from host arrays (pageable or pinned). */
+/* Same as bps_set_data from host arrays (pageable or pinned).  Subsamples are
+ * copied one at a time through two device staging slots on copy streams, the
+ * copy of one overlapping the check of the previous. */
 bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R);
+
+/* Same with the counts as uint16 [n_sub][N][N][N] (the library's own storage
+ * width; counts are bounded by 65535 in any case): a quarter less to copy. */
+bps_status bps_set_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R);
 
 /* Chain state (Sec. 3.2): delta_dev float32 [N][N][N] real field (its mean is
  * dropped: the k = 0 mode is held at zero), P [n_bins], b [n_sub], nbar [n_sub]

@@ -43,6 +43,7 @@ _SIGS = {
                     ctypes.POINTER(_P)], ctypes.c_int),
     "bps_set_data": ([_P, _P, _P], ctypes.c_int),
     "bps_set_data_host": ([_P, _P, _P], ctypes.c_int),
+    "bps_set_data_host_u16": ([_P, _P, _P], ctypes.c_int),
     "bps_set_state": ([_P, _P, _D, _D, _D, ctypes.c_uint64], ctypes.c_int),
     "bps_get_state": ([_P, _P, _D, _D, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "bps_get_spectrum": ([_P, _P], ctypes.c_int),
@@ -168,6 +169,12 @@ def bps_set_data_host(ctx, counts, R):
     c = np.ascontiguousarray(counts, dtype=np.int32)
     r = np.ascontiguousarray(R, dtype=np.float32)
     _check(ctx, load().bps_set_data_host(ctx, c.ctypes.data_as(_P), r.ctypes.data_as(_P)))
+
+
+def bps_set_data_host_u16(ctx, counts, R):
+    c = np.ascontiguousarray(counts, dtype=np.uint16)
+    r = np.ascontiguousarray(R, dtype=np.float32)
+    _check(ctx, load().bps_set_data_host_u16(ctx, c.ctypes.data_as(_P), r.ctypes.data_as(_P)))
 
 
 def bps_set_state(ctx, delta, P, b, nbar, iteration=0):

@@ -634,7 +634,7 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
 }
 
 // ------------------------------------------------------------------ per-chain operations
-bps_status set_data_chain(bps_ctx* ctx, int ch, const int32_t* counts, const float* R, bool host) {
+bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float* R, bool host, bool c16 = false) {
   if (!counts || !R) return fail(ctx, BPS_EINVAL, "null argument");
   cudaStream_t s = ctx->stream;
   const int ns = ctx->nsub[ch];
@@ -675,16 +675,17 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const int32_t* counts, const flo
   if ((long long)ns * 4 * blocks > ctx->part_cstride) return fail(ctx, BPS_EINVAL, "too many subsamples");
   if (host) CK(cudaEventRecord(ctx->stage_free[0], s));   // orders the copies after earlier work on s
   if (host) CK(cudaEventRecord(ctx->stage_free[1], s));
+  const size_t csz = c16 ? sizeof(uint16_t) : sizeof(int32_t);
   for (int l = 0; l < ns; ++l) {
-    const int32_t* cl = counts + (size_t)l * ctx->nv;
+    const void* cl = static_cast<const char*>(counts) + (size_t)l * ctx->nv * csz;
     const float* rl = R + (size_t)l * ctx->nv;
     if (host) {
       // copy subsample l into slot l % 2 once the data kernel of subsample l - 2 has read it
       const int sl = l & 1;
-      int32_t* ctmp = reinterpret_cast<int32_t*>(ctx->stage + sl * slot_bytes);
+      void* ctmp = ctx->stage + sl * slot_bytes;
       float* rtmp = reinterpret_cast<float*>(ctx->stage + sl * slot_bytes + (size_t)ctx->nv * sizeof(int32_t));
       for (int k = 0; k < 2; ++k) CK(cudaStreamWaitEvent(ctx->copy_stream[k], ctx->stage_free[sl], 0));
-      CK(cudaMemcpyAsync(ctmp, cl, ctx->nv * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->copy_stream[0]));
+      CK(cudaMemcpyAsync(ctmp, cl, ctx->nv * csz, cudaMemcpyHostToDevice, ctx->copy_stream[0]));
       CK(cudaMemcpyAsync(rtmp, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_stream[1]));
       for (int k = 0; k < 2; ++k) {
         CK(cudaEventRecord(ctx->stage_copied[sl][k], ctx->copy_stream[k]));
@@ -693,8 +694,12 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const int32_t* counts, const flo
       cl = ctmp;
       rl = rtmp;
     }
-    launch_data(cl, rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv, ctx->nv,
-                part + (size_t)l * 4 * blocks, blocks, blocks, s);
+    if (c16)
+      launch_data16(static_cast<const uint16_t*>(cl), rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv,
+                    ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, s);
+    else
+      launch_data(static_cast<const int32_t*>(cl), rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv,
+                  ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, s);
     LAUNCHED(ctx, 1);
     if (host) CK(cudaEventRecord(ctx->stage_free[l & 1], s));
   }
@@ -1021,6 +1026,11 @@ bps_status bps_set_data(bps_ctx* ctx, const int32_t* counts_dev, const float* R_
 bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R) {
   if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
   return set_data_chain(ctx, 0, counts, R, true);
+}
+
+bps_status bps_set_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R) {
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
+  return set_data_chain(ctx, 0, counts, R, true, true);
 }
 
 bps_status bps_set_state(bps_ctx* ctx, const float* delta_dev, const double* P, const double* b, const double* nbar,

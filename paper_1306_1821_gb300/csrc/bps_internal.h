@@ -42,6 +42,9 @@ bool pass_table(int N, PassTable* out);
 void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int nch, cudaStream_t s);
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
                  int stride, int blocks, cudaStream_t s);
+// the same from 16-bit counts
+void launch_data16(const uint16_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
+                   int stride, int blocks, cudaStream_t s);
 void launch_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
                          uint64_t* out, cudaStream_t s);
 void launch_voxel_normals(uint64_t seed, uint64_t it, size_t n, float* out, cudaStream_t s);

@@ -747,29 +747,41 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
 }
 
 // Data check and compression: counts int32 -> uint16, R copied; per block the
-// sums R, N^2/R, #(R>0) over R > 0 and the number of invalid voxels.
-__global__ void __launch_bounds__(256) k_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout,
+// sums R, N^2/R, #(R>0) over R > 0 and the number of invalid voxels.  Per
+// thread the sums run in FP32 with Kahan compensation and the counts in
+// integers (FP64 arithmetic is slow on this part); blocks combine in FP64.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, uint16_t* cout, float* rout,
                                               long long nv, double* part, int stride) {
   __shared__ double s_red[32];
-  double sR = 0.0, sB = 0.0, no = 0.0, bad = 0.0;
+  float sR = 0.f, cR = 0.f, sB = 0.f, cB = 0.f;
+  unsigned int no = 0, bad = 0;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nv; i += (long long)gridDim.x * 256) {
     const float r = rin[i];
-    const int n = cin[i];
+    const int n = (int)cin[i];
     const bool rok = (r >= 0.f) && isfinite(r);
     const bool nok = n >= 0 && n <= 65535;
-    if (!rok || !nok || (r == 0.f && n > 0)) bad += 1.0;
+    if (!rok || !nok || (r == 0.f && n > 0)) ++bad;
     cout[i] = (uint16_t)(nok ? n : 0);
     rout[i] = rok ? r : 0.f;
     if (rok && r > 0.f) {
-      sR += r;
-      sB += (double)n * (double)n / (double)r;
-      no += 1.0;
+      kahan_add(sR, cR, r);
+      const float fn = (float)(nok ? n : 0);
+      kahan_add(sB, cB, fn * fn / r);
+      ++no;
     }
   }
-  double v0 = block_sum<256>(sR, s_red);
-  double v1 = block_sum<256>(sB, s_red);
-  double v2 = block_sum<256>(no, s_red);
-  double v3 = block_sum<256>(bad, s_red);
+  double v0 = block_sum<256>((double)sR - (double)cR, s_red);
+  double v1 = block_sum<256>((double)sB - (double)cB, s_red);
+  double v2 = block_sum<256>((double)no, s_red);
+  double v3 = block_sum<256>((double)bad, s_red);
   if (threadIdx.x == 0) {
     part[0 * stride + blockIdx.x] = v0;
     part[1 * stride + blockIdx.x] = v1;
@@ -881,7 +893,11 @@ void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int 
 }
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
                  int stride, int blocks, cudaStream_t s) {
-  k_data<<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride);
+  k_data<int32_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride);
+}
+void launch_data16(const uint16_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
+                   int stride, int blocks, cudaStream_t s) {
+  k_data<uint16_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride);
 }
 void launch_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
                          uint64_t* out, cudaStream_t s) {

@@ -268,6 +268,14 @@ def test_host_upload_equals_device_upload(torch_cuda):
         ra = bps.bps_gibbs_iterate(a.ctx, 2, a.rec_len)
         rb = bps.bps_gibbs_iterate(b.ctx, 2, b.rec_len)
         assert np.array_equal(ra, rb)
+        # 16-bit counts from the host: the same data, the same chain
+        c = pb.gpu(seed=13, jump=1)
+        try:
+            bps.bps_set_data_host_u16(c.ctx, pb.counts.astype(np.uint16), pb.R)
+            rc = bps.bps_gibbs_iterate(c.ctx, 2, c.rec_len)
+            assert np.array_equal(ra, rc)
+        finally:
+            c.close()
         bad = pb.counts.copy()
         bad[2, 0, 0, 0] = -1
         with pytest.raises(bps.BpsError):
