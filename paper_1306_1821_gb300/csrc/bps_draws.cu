@@ -158,6 +158,31 @@ __device__ double gig_dphi(double y, double lam, double om, double m) {
   return 1.0 / (y - m) + 0.5 * ((lam - 1.0) / y - 0.5 * om + 0.5 * om / (y * y));
 }
 
+// Root of gig_dphi in (lo, hi), found by the 32 lanes of a warp together:
+// each round evaluates 32 interior points, keeps the one gap where the sign
+// turns and shrinks the interval 33-fold (12 rounds reach FP64 resolution).
+// `neg_right`: the right-hand side of the root is where gig_dphi < 0 (else
+// where it is <= 0).  All lanes return the same value.
+__device__ double warp_root(double lo, double hi, bool neg_right, double lam, double om, double m) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < 16; ++round) {
+    const double w = (hi - lo) / 33.0;
+    if (!(w > 0.0)) break;
+    const double x = lo + w * (double)(lane + 1);
+    const double d = gig_dphi(x, lam, om, m);
+    const unsigned right = __ballot_sync(0xffffffffu, neg_right ? (d < 0.0) : !(d > 0.0));
+    const int k = right ? __ffs(right) - 1 : 32;        // first point on the right-hand side
+    const double nlo = lo + w * (double)k;
+    const double nhi = k == 32 ? hi : lo + w * (double)(k + 1);
+    if (!(nlo > lo || nhi < hi)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Called by all 32 lanes of one warp (identical arguments); every lane returns
+// the same draw.
 __device__ double gig_draw(double p, double A, double B, uint64_t seed, uint64_t it, int l, int* fail) {
   const double lam = fabs(p);
   const double om = sqrt(A * B);
@@ -171,24 +196,9 @@ __device__ double gig_draw(double p, double A, double B, uint64_t seed, uint64_t
     step *= 2.0;
     hi = m + step;
   }
-  double lo = m;
-  for (int i = 0; i < 200; ++i) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (gig_dphi(mid, lam, om, m) > 0.0) lo = mid;
-    else hi = mid;
-  }
-  const double yp = 0.5 * (lo + hi);
+  const double yp = warp_root(m, hi, false, lam, om, m);
   const double vp = (yp - m) * exp(0.5 * gig_logh(yp, lam, om, m));
-  lo = 0.0;
-  hi = m;
-  for (int i = 0; i < 200; ++i) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (gig_dphi(mid, lam, om, m) < 0.0) hi = mid;
-    else lo = mid;
-  }
-  const double ym = 0.5 * (lo + hi);
+  const double ym = warp_root(0.0, m, true, lam, om, m);
   const double vm = ym > 0.0 ? (ym - m) * exp(0.5 * gig_logh(ym, lam, om, m)) : -m;
   double y = m;
   bool ok = false;
@@ -218,11 +228,25 @@ __global__ void k_bias_nbar(ScalarArgs a0, int region, int nz) {
   if (l >= ds->nsub) return;
   double S[3];
   for (int q = 0; q < 3; ++q) S[q] = sum_partials(a.part + region + (size_t)(3 * l + q) * a.stride, nz, sh);
+  // the sums are valid in thread 0: hand them to the first warp, which draws
+  // together (the GIG bounds are found lane-parallel); lane 0 writes
   if (threadIdx.x == 0) {
+    sh[0] = S[0];
+    sh[1] = S[1];
+    sh[2] = S[2];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    S[0] = sh[0];
+    S[1] = sh[1];
+    S[2] = sh[2];
+    const bool lead = threadIdx.x == 0;
     const uint64_t it = ds->iteration;
-    ds->sums[l][0] = S[0];
-    ds->sums[l][1] = S[1];
-    ds->sums[l][2] = S[2];
+    if (lead) {
+      ds->sums[l][0] = S[0];
+      ds->sums[l][1] = S[1];
+      ds->sums[l][2] = S[2];
+    }
     double b = ds->b[l];
     const double nb = ds->nbar[l];
     int fail = 0;
@@ -239,11 +263,13 @@ __global__ void k_bias_nbar(ScalarArgs a0, int region, int nz) {
     double x = nb;
     if (A > 0.0 && ds->sumB[l] > 0.0) x = gig_draw(p, A, ds->sumB[l], ds->seed, it, l, &fail);
     else fail = 1;
-    if (fail || !isfinite(b) || !isfinite(x)) {
-      atomicOr(&ds->status, ST_DRAW_FAIL);
-    } else {
-      ds->b[l] = b;
-      ds->nbar[l] = x;
+    if (lead) {
+      if (fail || !isfinite(b) || !isfinite(x)) {
+        atomicOr(&ds->status, ST_DRAW_FAIL);
+      } else {
+        ds->b[l] = b;
+        ds->nbar[l] = x;
+      }
     }
   }
 }

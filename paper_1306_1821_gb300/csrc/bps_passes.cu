@@ -709,6 +709,14 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
 }
 
 // ------------------------------------------------------------------ voxel kernels
+// Kahan-compensated FP32 running sum (s, c); the sum is s - c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 // a_i = sum_l b_l^2 Nbar_l R^l_i,  c_i = sum_l b_l (N^l_i - Nbar_l R^l_i)  (Eq. Wiener_Posterior_force);
 // the counts are zero wherever R = 0 (checked by set_data), so no mask is needed.
 __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int region) {
@@ -724,7 +732,7 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
     s_bn[threadIdx.x] = (float)(b * nb);
   }
   __syncthreads();
-  double acc = 0.0;
+  float acc = 0.f, comp = 0.f;   // FP32 with Kahan compensation per thread; FP64 across the block
   const long long n4 = nv / 4;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Cc = A;
@@ -740,9 +748,9 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
     }
     reinterpret_cast<float4*>(fp.a)[i] = A;
     reinterpret_cast<float4*>(fp.c)[i] = Cc;
-    acc += (double)A.x + (double)A.y + (double)A.z + (double)A.w;
+    kahan_add(acc, comp, (A.x + A.y) + (A.z + A.w));
   }
-  double s = block_sum<256>(acc, s_red);
+  double s = block_sum<256>((double)acc - (double)comp, s_red);
   if (threadIdx.x == 0) fp.part[region + blockIdx.x] = s;
 }
 
@@ -750,13 +758,6 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
 // sums R, N^2/R, #(R>0) over R > 0 and the number of invalid voxels.  Per
 // thread the sums run in FP32 with Kahan compensation and the counts in
 // integers (FP64 arithmetic is slow on this part); blocks combine in FP64.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
 template <typename CT>
 __global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, uint16_t* cout, float* rout,
                                               long long nv, double* part, int stride) {
