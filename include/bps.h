@@ -332,6 +332,15 @@ uint64_t bps_kernel_launches(const bps_ctx* ctx);
 bps_status bps_profile(bps_ctx* ctx, int enable);
 bps_status bps_profile_read(bps_ctx* ctx, double* ms, uint64_t* n);
 
+/* Line pairs per tile (4, 8 or 16) of the force z pass of ctx (the first
+ * group of a batch).  Chosen when the context is created: the first context of
+ * a (GPU model, grid, number of chains) kind times the three tile sizes on its
+ * own buffers and keeps the fastest; the choice is cached for the process and
+ * in the JSON file named by BPS_TUNE_CACHE (default $HOME/.cache/bps_tune.json),
+ * so that later contexts and runs reuse it.  BPS_AUTOTUNE=0 keeps 8.  The tile
+ * size changes only the grouping of the likelihood-energy partial sums. */
+int bps_z_line_pairs(const bps_ctx* ctx);
+
 void bps_destroy(bps_ctx* ctx);
 
 #ifdef __cplusplus

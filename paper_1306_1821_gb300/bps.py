@@ -44,6 +44,7 @@ _SIGS = {
     "bps_set_data": ([_P, _P, _P], ctypes.c_int),
     "bps_set_data_host": ([_P, _P, _P], ctypes.c_int),
     "bps_set_data_host_u16": ([_P, _P, _P], ctypes.c_int),
+    "bps_z_line_pairs": ([_P], ctypes.c_int),
     "bps_set_state": ([_P, _P, _D, _D, _D, ctypes.c_uint64], ctypes.c_int),
     "bps_get_state": ([_P, _P, _D, _D, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "bps_get_spectrum": ([_P, _P], ctypes.c_int),
@@ -428,6 +429,10 @@ def bps_get_mass_scale(ctx, chain=0):
     out = np.zeros(64)
     _check(ctx, load().bps_get_mass_scale(ctx, int(chain), ctypes.byref(n), out.ctypes.data_as(_D)))
     return out[:n.value].copy()
+
+
+def bps_z_line_pairs(ctx):
+    return int(load().bps_z_line_pairs(ctx))
 
 
 def bps_version():

@@ -11,10 +11,15 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
+
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include "bps_internal.h"
 #include "bps_passes.cuh"
@@ -54,6 +59,11 @@ struct bps_ctx {
   int chain_cap = 0;
   double* host_buf = nullptr;   // pinned staging for small reads
   int n_mass = 0;
+  // the force z pass in use (line pairs per tile chosen by the autotuner) and
+  // the number of likelihood-energy partials it writes
+  void (*zgrad)(const Fields&, int region, int nch, cudaStream_t) = nullptr;
+  int zgrad_tiles = 0;
+  int zgrad_pairs = 8;
   MassNet* mnet = nullptr;      // network mass (bps_set_mass_net): scales recomputed before every move
   std::vector<char> have_data;
   int rebuild_blocks = 0;
@@ -320,7 +330,7 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   P.y_fwd(f, BUF_PH, B, s);
   P.x_init(f, region_offset(ctx, RG_INIT), B, s);
   P.y_inv(f, BUF_W, B, s);
-  P.z_grad(f, region_offset(ctx, RG_LIK0), B, s);
+  ctx->zgrad(f, region_offset(ctx, RG_LIK0), B, s);
   P.y_fwd(f, BUF_W, B, s);
   for (int st = 1; st <= L; ++st) {
     prof_mark(ctx, 0);
@@ -330,7 +340,7 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
     P.y_inv(f, BUF_W, B, s);
     prof_mark(ctx, 1);
     prof_mark(ctx, 2);
-    P.z_grad(f, st == L ? region_offset(ctx, RG_LIK1) : -1, B, s);
+    ctx->zgrad(f, st == L ? region_offset(ctx, RG_LIK1) : -1, B, s);
     prof_mark(ctx, 2);
     prof_mark(ctx, 3);
     P.y_fwd(f, BUF_W, B, s);
@@ -338,7 +348,7 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   }
   P.x_final(f, region_offset(ctx, RG_FINAL), B, s);
   launch_move_end(sa, region_offset(ctx, RG_INIT), region_offset(ctx, RG_LIK0), region_offset(ctx, RG_FINAL),
-                  region_offset(ctx, RG_LIK1), P.x_tiles, P.z_tiles, B, s);
+                  region_offset(ctx, RG_LIK1), P.x_tiles, ctx->zgrad_tiles, B, s);
   int n = 9 + 4 * L + (ctx->mnet ? 1 : 0);
   if (advance) {
     launch_advance(ctx->ds, B, s);
@@ -392,10 +402,11 @@ bps_status jump_gradient(bps_ctx* ctx) {
   const int B = ctx->batch;
   P.x_jinv(f, B, s);
   P.y_inv(f, BUF_W, B, s);
-  P.z_grad(f, region_offset(ctx, RG_JLIK), B, s);
+  ctx->zgrad(f, region_offset(ctx, RG_JLIK), B, s);
   P.y_fwd(f, BUF_W, B, s);
   P.x_jgrad(f, region_offset(ctx, RG_JGRAD), B, s);
-  launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), P.z_tiles, B, s);
+  launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), ctx->zgrad_tiles, B,
+                     s);
   LAUNCHED(ctx, 6);
   return BPS_OK;
 }
@@ -518,6 +529,118 @@ void free_all(bps_ctx* c) {
   if (c->host_buf) cudaFreeHost(c->host_buf);
 }
 
+// ------------------------------------------------------------------ tile autotuner
+// The force z pass can run with 4, 8 or 16 line pairs per tile; which is
+// fastest depends on the grid and on how many chains share a launch.  The
+// first context of a (GPU, N, chains) kind times each candidate on its own
+// buffers (before any data is set: W is scratch) and keeps the fastest; the
+// choice is cached for the process and in a JSON file (BPS_TUNE_CACHE, else
+// $HOME/.cache/bps_tune.json) so later runs reuse it and give the same
+// chains.  BPS_AUTOTUNE=0 keeps 8 line pairs.  The choice changes only the
+// grouping of the likelihood-energy partial sums (FP64 sums of FP32 terms).
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_path() {
+  if (const char* p = std::getenv("BPS_TUNE_CACHE")) return p;
+  if (const char* h = std::getenv("HOME")) return std::string(h) + "/.cache/bps_tune.json";
+  return "";
+}
+
+// flat JSON object of string keys and integer values
+void tune_load() {
+  g_tune_loaded = true;
+  const std::string path = tune_path();
+  if (path.empty()) return;
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+  std::fclose(f);
+  size_t i = 0;
+  while ((i = txt.find('"', i)) != std::string::npos) {
+    const size_t j = txt.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const std::string key = txt.substr(i + 1, j - i - 1);
+    const size_t c = txt.find(':', j);
+    if (c == std::string::npos) break;
+    g_tune[key] = std::atoi(txt.c_str() + c + 1);
+    i = txt.find_first_of(",}", c);
+    if (i == std::string::npos) break;
+  }
+}
+
+void tune_save() {
+  const std::string path = tune_path();
+  if (path.empty()) return;
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos) mkdir(path.substr(0, slash).c_str(), 0755);   // one level; failure is harmless
+  const std::string tmp = path + ".tmp." + std::to_string((long long)getpid());
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{");
+  bool first = true;
+  for (const auto& kv : g_tune) {
+    std::fprintf(f, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
+    first = false;
+  }
+  std::fprintf(f, "\n}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+bps_status choose_zgrad(bps_ctx* ctx) {
+  int pick = 1;   // 8 line pairs
+  const char* e = std::getenv("BPS_AUTOTUNE");
+  if (!(e && std::atoi(e) == 0)) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    const std::string key = std::string(prop.name) + " N=" + std::to_string(ctx->N) + " chains=" +
+                            std::to_string(ctx->batch) + " zpairs";
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_loaded) tune_load();
+    auto it = g_tune.find(key);
+    int lp = it != g_tune.end() ? it->second : 0;
+    if (lp == 4 || lp == 8 || lp == 16) {
+      pick = lp == 4 ? 0 : lp == 8 ? 1 : 2;
+    } else {
+      cudaStream_t s = ctx->stream;
+      Fields f = fields(ctx);
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int c = 0; c < 3; ++c) {
+        for (int w = 0; w < 2; ++w) ctx->pt.z_grad_lp[c](f, -1, ctx->batch, s);
+        CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 5; ++r) ctx->pt.z_grad_lp[c](f, -1, ctx->batch, s);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          pick = c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      CK(cudaGetLastError());
+      g_tune[key] = 4 << pick;
+      tune_save();
+    }
+  }
+  ctx->zgrad = ctx->pt.z_grad_lp[pick];
+  ctx->zgrad_tiles = ctx->pt.z_lp_tiles[pick];
+  ctx->zgrad_pairs = 4 << pick;
+  return BPS_OK;
+}
+
 // ------------------------------------------------------------------ group construction
 bps_status check_config(const bps_config* cfg, int min_sub) {
   if (cfg->n_bins < 1 || cfg->n_bins > MAXB) return fail(nullptr, BPS_EINVAL, "n_bins must be in 1..64");
@@ -584,7 +707,7 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
   ctx->n_sm = sms > 0 ? sms : 148;
   // the voxel kernels of a batch run B chains side by side: fewer blocks each
   ctx->rebuild_blocks = std::max(1, std::min(4 * ctx->n_sm / B + 1, (int)(ctx->nv / 1024) + 1));
-  ctx->part_stride = std::max(std::max(pt.x_tiles, pt.z_tiles), ctx->rebuild_blocks);
+  ctx->part_stride = std::max(std::max(std::max(pt.x_tiles, pt.z_tiles), pt.z_lp_tiles[0]), ctx->rebuild_blocks);
   ctx->part_cstride = (long long)region_total() * ctx->part_stride;
 
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
@@ -625,6 +748,12 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     std::string msg = std::string("initialisation failed: ") + cudaGetErrorString(e);
+    free_all(ctx);
+    delete ctx;
+    return fail(nullptr, BPS_ECUDA, msg);
+  }
+  if (choose_zgrad(ctx) != BPS_OK) {
+    std::string msg = "tile autotuning failed: " + ctx->err;
     free_all(ctx);
     delete ctx;
     return fail(nullptr, BPS_ECUDA, msg);
@@ -981,6 +1110,11 @@ uint64_t bps_kernel_launches(const bps_ctx* ctx) {
   return n;
 }
 
+int bps_z_line_pairs(const bps_ctx* ctx) {
+  if (!ctx) return 0;
+  return ctx->is_batch ? (ctx->groups.empty() ? 0 : ctx->groups[0]->zgrad_pairs) : ctx->zgrad_pairs;
+}
+
 bps_status bps_profile(bps_ctx* ctx, int enable) {
   if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
   if (ctx->is_batch) return fail(ctx, BPS_EINVAL, "kernel timing is per single-chain context");
@@ -1285,12 +1419,12 @@ bps_status bps_gradient(bps_ctx* ctx, float* grad_dev, double* energies) {
   launch_move_begin(sa, 1, s);   // per-bin tables of the current P and abar
   ctx->pt.x_inv(f, -1, ctx->W, 1, s);
   ctx->pt.y_inv(f, BUF_W, 1, s);
-  ctx->pt.z_grad(f, region_offset(ctx, RG_LIK0), 1, s);
+  ctx->zgrad(f, region_offset(ctx, RG_LIK0), 1, s);
   ctx->pt.y_fwd(f, BUF_W, 1, s);
   ctx->pt.x_grad(f, ctx->W, region_offset(ctx, RG_GRAD), 1, s);
   double* scratch = reinterpret_cast<double*>(ds_addr(ctx, 0, DS_OFF(scratch)));
   launch_reduce_to(sa, region_offset(ctx, RG_GRAD), ctx->pt.x_tiles, 1, 0.5 / (double)ctx->nv, scratch, s);
-  launch_reduce_to(sa, region_offset(ctx, RG_LIK0), ctx->pt.z_tiles, 1, 1.0, scratch + 1, s);
+  launch_reduce_to(sa, region_offset(ctx, RG_LIK0), ctx->zgrad_tiles, 1, 1.0, scratch + 1, s);
   LAUNCHED(ctx, 8);
   st = copy_spec_out(ctx, ctx->W, grad_dev);
   if (st != BPS_OK) return st;

@@ -36,6 +36,10 @@ struct PassTable {
   void (*z_r2c)(const Fields&, const float* rin, float2* dst, cudaStream_t);   // one chain
   void (*z_c2r)(const Fields&, const float2* src, float* rout, cudaStream_t);  // one chain
   void (*z_sums)(const Fields&, int region, int nch, cudaStream_t);
+  // z_grad with 4, 8 or 16 line pairs per tile (autotuned per grid) and the
+  // number of tiles (likelihood-energy partials) of each
+  void (*z_grad_lp[3])(const Fields&, int region, int nch, cudaStream_t);
+  int z_lp_tiles[3];
 };
 
 bool pass_table(int N, PassTable* out);

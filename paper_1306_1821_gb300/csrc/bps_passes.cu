@@ -495,11 +495,11 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_YPASS_MIN_BLOCKS) k_ypass(Fiel
 // LP pairs of consecutive z lines per tile; line 2f is the real part and line
 // 2f+1 the imaginary part of one complex transform of length N.  The lines of
 // the tile are contiguous in HBM and arrive by bulk copies.
-template <int N, int MODE>
+template <int N, int MODE, int LP = Cfg<N>::LP>
 struct ZSmem {
   using C = Cfg<N>;
-  static constexpr int LINES = 2 * C::LP;
-  static constexpr size_t BUF = (size_t)C::LP * (N + C::RMAX) * sizeof(float2);
+  static constexpr int LINES = 2 * LP;
+  static constexpr size_t BUF = (size_t)LP * (N + C::RMAX) * sizeof(float2);
   static constexpr size_t AC = MODE == Z_GRAD ? (size_t)LINES * N * sizeof(float) : 0;
   static constexpr size_t OFF_BUF = 0;
   static constexpr size_t OFF_A = BUF;
@@ -512,12 +512,12 @@ struct ZSmem {
   static_assert(BUF >= (size_t)LINES * N * sizeof(float), "staging does not fit");
 };
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
+template <int N, int MODE, int LP = Cfg<N>::LP>
+__global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs za) {
   const Fields fp = at_chain(fp0, blockIdx.y);
   using C = Cfg<N>;
-  using L = ZSmem<N, MODE>;
-  constexpr int R1 = C::R1, R2 = C::R2, H = C::H, ZP = C::ZP, NTZ = C::NTZ;
+  using L = ZSmem<N, MODE, LP>;
+  constexpr int R1 = C::R1, R2 = C::R2, H = C::H, ZP = C::ZP, NTZ = LP * C::RMAX;
   constexpr int LINES = L::LINES;
   extern __shared__ __align__(128) unsigned char smem[];
   float2* s_buf = reinterpret_cast<float2*>(smem + L::OFF_BUF);
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
   if constexpr (MODE == Z_GRAD || MODE == Z_C2R || MODE == Z_SUMS) {
     {
       const int f = t / R2, a = t % R2;
-      if (f < C::LP) {
+      if (f < LP) {
 #pragma unroll
         for (int b = 0; b < R1; ++b) {
           const int k = a + R2 * b;
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
       }
     }
     __syncthreads();
-    fft2<N, R2, R1, INV, MAP_ROW, C::LP>(v, s_buf, s_tw, t);
+    fft2<N, R2, R1, INV, MAP_ROW, LP>(v, s_buf, s_tw, t);
   } else {
     float* sr = reinterpret_cast<float*>(s_buf);
     if constexpr (MODE == Z_NOISE) {
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
       __syncthreads();
     }
     const int f = t / R1, c = t % R1;
-    if (f < C::LP) {
+    if (f < LP) {
 #pragma unroll
       for (int d = 0; d < R2; ++d) {
         const int n = c + R1 * d;
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
     const int f = t / R1, c = t % R1;
     const long long la = (L0 + 2 * f) * N, lb = la + N;
     if constexpr (MODE == Z_C2R) {
-      if (f < C::LP) {
+      if (f < LP) {
 #pragma unroll
         for (int d = 0; d < R2; ++d) {
           const int n = c + R1 * d;
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
       const int nsub = ds->nsub;
       for (int l = 0; l < nsub; ++l) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        if (f < C::LP) {
+        if (f < LP) {
           const uint16_t* cn = fp.cnt + l * nv;
           const float* rr = fp.R + l * nv;
 #pragma unroll
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
     // Z_GRAD: the local force g = a delta - c (Eq. Wiener_Posterior_force) and the
     // likelihood energy (1/2) sum (a delta^2 - 2 c delta)
     float e = 0.f;
-    if (f < C::LP) {
+    if (f < LP) {
       const int ra = (2 * f) * N, rb = ra + N;
 #pragma unroll
       for (int d = 0; d < R2; ++d) {
@@ -686,10 +686,10 @@ __global__ void __launch_bounds__(Cfg<N>::NTZ) k_zpass(Fields fp0, ZArgs za) {
   }
 
   // forward transform of the packed pair, then split into the two half spectra
-  fft2<N, R1, R2, FWD, MAP_ROW, C::LP>(v, s_buf, s_tw, t);
+  fft2<N, R1, R2, FWD, MAP_ROW, LP>(v, s_buf, s_tw, t);
   {
     const int f = t / R2, c = t % R2;
-    if (f < C::LP) {
+    if (f < LP) {
 #pragma unroll
       for (int d = 0; d < R1; ++d) s_buf[f * N + c + R2 * d] = v[d];
     }
@@ -829,16 +829,18 @@ struct Launch {
   static void y(const Fields& fp, int buf, int nch, cudaStream_t s) {
     k_ypass<N, D><<<dim3(C::TILES, nch), C::NT, 0, s>>>(fp, buf);
   }
-  template <int M>
+  template <int M, int LP = C::LP>
   static void z(const Fields& fp, const ZArgs& za, int nch, cudaStream_t s) {
-    k_zpass<N, M><<<dim3(C::ZTILES, nch), C::NTZ, ZSmem<N, M>::BYTES, s>>>(fp, za);
+    k_zpass<N, M, LP><<<dim3(N * N / (2 * LP), nch), LP * C::RMAX, ZSmem<N, M, LP>::BYTES, s>>>(fp, za);
   }
-  template <int M>
+  template <int M, int LP = C::LP>
   static void zattr() {
-    cudaFuncSetAttribute(k_zpass<N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZSmem<N, M>::BYTES);
+    cudaFuncSetAttribute(k_zpass<N, M, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ZSmem<N, M, LP>::BYTES);
   }
   static void attrs() {
     zattr<Z_GRAD>(); zattr<Z_NOISE>(); zattr<Z_R2C>(); zattr<Z_C2R>(); zattr<Z_SUMS>();
+    zattr<Z_GRAD, 4>(); zattr<Z_GRAD, 16>();
   }
 };
 
@@ -869,6 +871,11 @@ static PassTable make_table() {
   T.y_fwd = [](const Fields& f, int buf, int n, cudaStream_t s) { L::template y<FWD>(f, buf, n, s); };
   T.y_inv = [](const Fields& f, int buf, int n, cudaStream_t s) { L::template y<INV>(f, buf, n, s); };
   T.z_grad = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_GRAD>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
+  // the force z pass at every tile size the autotuner chooses from
+  T.z_grad_lp[0] = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_GRAD, 4>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
+  T.z_grad_lp[1] = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_GRAD, 8>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
+  T.z_grad_lp[2] = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_GRAD, 16>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
+  for (int i = 0; i < 3; ++i) T.z_lp_tiles[i] = N * N / (2 * (4 << i));
   T.z_noise = [](const Fields& f, int n, cudaStream_t s) { L::template z<Z_NOISE>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, -1, 0}, n, s); };
   T.z_r2c = [](const Fields& f, const float* rin, float2* dst, cudaStream_t s) { L::template z<Z_R2C>(f, ZArgs{nullptr, dst, rin, nullptr, -1, 0}, 1, s); };
   T.z_c2r = [](const Fields& f, const float2* src, float* rout, cudaStream_t s) { L::template z<Z_C2R>(f, ZArgs{src, nullptr, nullptr, rout, -1, 0}, 1, s); };

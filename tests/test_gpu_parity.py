@@ -283,3 +283,25 @@ def test_host_upload_equals_device_upload(torch_cuda):
     finally:
         a.close()
         b.close()
+
+
+def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
+    from paper_1306_1821_gb300 import bps
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("BPS_TUNE_CACHE", str(path))
+    cfg = bps.make_config(2, n_leapfrog=2, eps_max=0.1)
+    batch = bps.bps_create_batch([8, 8, 8], [100.0, 100.0, 100.0], [1, 1, 1], cfg)   # a kind no other test makes
+    try:
+        lp = bps.bps_z_line_pairs(batch)
+        assert lp in (4, 8, 16)
+    finally:
+        bps.bps_destroy(batch)
+    import json
+    cache = json.loads(path.read_text())
+    assert any(k.endswith("N=8 chains=3 zpairs") and v == lp for k, v in cache.items())
+    monkeypatch.setenv("BPS_AUTOTUNE", "0")
+    s = bps.Sampler(8, 100.0, 1, 2)
+    try:
+        assert bps.bps_z_line_pairs(s.ctx) == 8
+    finally:
+        s.close()

@@ -199,3 +199,35 @@ def test_gibbs_with_network_mass_matches_oracle_chain():
     finally:
         net.close()
         s.close()
+
+
+def test_invalid_preconditioner_arguments_are_rejected():
+    from paper_1306_1821_gb300 import bps
+    pb = Problem(16, n_sub=1, n_bins=4)
+    s = sampler(pb, 3, 0)
+    try:
+        with pytest.raises(bps.BpsError):
+            bps.bps_mass_stats(s.ctx, 2, 60)                 # a mass bin with no mode at 16^3
+        with pytest.raises(bps.BpsError):
+            bps.bps_set_mass_scale(s.ctx, np.array([1.0, -2.0]))
+        net = bps.MLP([7, 8, 5])                              # input width must be 2 n_bins = 8
+        try:
+            with pytest.raises(bps.BpsError):
+                bps.bps_set_mass_net(s.ctx, net, np.zeros(7), np.ones(7), 2.0)
+        finally:
+            net.close()
+        net = bps.MLP([8, 8, 5])
+        try:
+            with pytest.raises(bps.BpsError):
+                bps.bps_set_mass_net(s.ctx, net, np.zeros(8), np.zeros(8), 2.0)   # zero feature scale
+            bps.bps_set_mass_net(s.ctx, net, np.zeros(8), np.ones(8), 2.0)
+            with pytest.raises(bps.BpsError):
+                bps.bps_mass_stats(s.ctx, 2, 3)                  # must equal the network's 5 outputs
+        finally:
+            net.close()
+    finally:
+        s.close()
+    with pytest.raises(bps.BpsError):
+        bps.MLP([8, 0, 5])
+    with pytest.raises(bps.BpsError):
+        bps.MLP([8, 8, 8, 8, 8, 8])                            # more than four layers
