@@ -499,13 +499,21 @@ def pk_ess(rec, n_bins, N, secs):
             "sd_lnP": [round(float(v), 4) for v in np.log(P).std(0)]}
 
 
+PRECOND_RUNS = {
+    # workload: (survey, training surveys, mass bins)
+    "precond128": ("survey128", 64, 64),
+    "precond256": ("survey256", 32, 64),
+}
+
+
 def run_precond(args):
-    """P(k) effective samples per second of the full sampler on the 128^3
-    six-subsample survey, with the plain diagonal mass and with the trained
-    network mass.  The network (32 -> 128 -> 128 -> 64, BF16 operands) is
-    trained on the device on statistics of 64 surveys with random caps and
-    spectra, in two rounds (the second on chains that already move with the
-    first round's mass); the 128^3 survey itself is held out."""
+    """P(k) effective samples per second of the full sampler with the plain
+    diagonal mass and with the trained network mass, on the 128^3 survey
+    (precond128) or the 256^3 survey of the headline (precond256).  The network
+    (2 n_bins -> 128 -> 128 -> 64, BF16 operands) is trained on the device on
+    statistics of random surveys of the same recipe (random caps and spectra),
+    in two rounds (the second on chains that already move with the first
+    round's mass); the benchmark survey itself is held out."""
     import numpy as np
     import torch
 
@@ -514,10 +522,11 @@ def run_precond(args):
         from paper_1306_1821_gb300 import build as b
         b.build()
     bps.load()
-    wl = inputs.WORKLOADS["survey128"]
-    n_mass, jeps = 64, 0.15
+    survey, n_train, n_mass = PRECOND_RUNS[args.workload]
+    wl = inputs.WORKLOADS[survey]
+    jeps = 0.15
     t0 = time.time()
-    probs = precond.random_problems(wl, 64, 5000, p_jitter=0.3)
+    probs = precond.random_problems(wl, n_train, 5000, p_jitter=0.3)
     F, T = precond.measure(probs, n_mass, n_moves=300, burn_in=100)
     pc = precond.Preconditioner(F.shape[1], n_mass)
     pc.fit(F, T, steps=2000, batch=64)
@@ -562,10 +571,11 @@ def run_precond(args):
         "n_gpus": 1, "steps": args.ess_iters, "warmup": max(args.warmup, 300),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
         "data": "synthetic",
-        "config": {"workload": "survey128: 128^3 grid, L=750 Mpc/h, six subsamples, 25% sky, exp(-(r/350)^2) "
-                               "radial selection, 16 k bins, 10 leapfrog steps, jump on (10 steps, "
-                               f"eps_max {jeps}); network 32-128-128-64 trained on 64 random surveys, "
-                               "the survey itself held out"},
+        "config": {"workload": f"{wl.name}: {wl.N}^3 grid, L={wl.box:g} Mpc/h, {wl.n_sub} subsamples, "
+                               f"{wl.f_sky:.0%} sky, {wl.radial} radial selection, {wl.n_bins} k bins, "
+                               f"{wl.n_leapfrog} leapfrog steps (eps_max {wl.eps_max}), jump on (10 steps, "
+                               f"eps_max {jeps}); network {2 * wl.n_bins}-128-128-{n_mass} trained on {n_train} "
+                               "random surveys of the same recipe, the survey itself held out"},
         "plain": arms["plain"], "network": arms["network"],
         "ratio_min_ess_per_s": arms["network"]["min_ess_per_s"] / arms["plain"]["min_ess_per_s"],
         "ratio_median_ess_per_s": arms["network"]["median_ess_per_s"] / arms["plain"]["median_ess_per_s"],
@@ -584,7 +594,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96", "precond128"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96", "precond128", "precond256"])
     ap.add_argument("--ess-iters", type=int, default=None,
                     help="Gibbs iterations of the P(k) ESS run (default 2000 at 256^3, 20000 per arm of precond128; "
                          "0 skips it)")
@@ -595,7 +605,7 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batch96":
         return run_batch(args)
-    if args.workload == "precond128":
+    if args.workload in PRECOND_RUNS:
         if args.ess_iters is None:
             args.ess_iters = 20000
         return run_precond(args)

@@ -1,6 +1,6 @@
 """Build of the CUDA library libbps.so for sm_103a (nvcc, in-tree, no cmake).
 
-The three translation units compile in parallel; the shared library links the
+The translation units compile in parallel; the shared library links the
 CUDA runtime dynamically so that it shares the process's runtime with PyTorch.
 """
 import os

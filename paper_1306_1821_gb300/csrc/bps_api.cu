@@ -45,7 +45,7 @@ struct bps_ctx {
   float2* dh[2] = {nullptr, nullptr};
   float2* ph = nullptr;
   float2* W = nullptr;
-  float2* acc = nullptr;      // running sum of the state (bps_batch_mass_stats), allocated on first use
+  float2* acc = nullptr;      // running sum of the state (bps_mass_stats), allocated on first use
   float* a = nullptr;
   float* c = nullptr;
   uint16_t* cnt = nullptr;

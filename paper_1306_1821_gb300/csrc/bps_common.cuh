@@ -269,7 +269,7 @@ struct DevState {
   int thr[MAXB];                     // smallest |n|^2 of each P bin
   int mthr[MAXB];                    // smallest |n|^2 of each mass-scale bin
   double scratch[8];                 // small results handed to the host
-  double mstat[MAXB], mstat2[MAXB];  // posterior statistics per mass bin (bps_batch_mass_stats)
+  double mstat[MAXB], mstat2[MAXB];  // posterior statistics per mass bin (bps_mass_stats)
   // per-chain constants (chains of one batch share the kernels, not these)
   double vc;                         // cell volume V_cell
   unsigned long long seed;           // Philox key
