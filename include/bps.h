@@ -73,7 +73,8 @@ typedef struct {
   double jump_eps_max;     /* step size bound of the jump's HMC */
   int fixed_bias_index;    /* bias held fixed (b-P degeneracy gauge); -1: none */
   int mass_mode;           /* 0: diagonal Fourier mass of Eq. Mass_matrix;
-                              1: that mass times per-bin scales (bps_set_mass_scale) */
+                              1: that mass times per-bin scales (bps_set_mass_scale);
+                              bps_set_mass_net installs a network mass in either mode */
   uint64_t seed;           /* Philox key */
 } bps_config;
 
@@ -87,7 +88,8 @@ typedef struct {
  * subsamples (Sec. 2, Sec. 3.3.2).  N in {8, 16, 32, 64, 96, 128, 256};
  * 1 <= n_sub <= 16.  cuda_stream is a cudaStream_t (NULL: the legacy default
  * stream).  Returns BPS_EINVAL for an unsupported N, a bin layout with an empty
- * bin, or out-of-range settings; BPS_ENOMEM if the device buffers do not fit. */
+ * bin, or out-of-range settings; BPS_ENOMEM if the device buffers do not fit.
+ * Creation also picks the tile size of the force z pass (bps_z_line_pairs). */
 bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* cfg,
                       void* cuda_stream, bps_ctx** out);
 
@@ -131,6 +133,17 @@ bps_status bps_set_spectrum(bps_ctx* ctx, const float* spec_dev);
  * n_leapfrog kick-drift-kick steps of size eps_max * u, Metropolis accept in
  * FP64 (Eq. acceptance_rule).  info may be NULL (then nothing synchronises). */
 bps_status bps_hmc_step(bps_ctx* ctx, bps_move_info* info);
+
+/* Burn-in adaptation of the step size (the paper's chains settle at about 92%
+ * acceptance after burn-in, Fig. accept_rat; it gives no tuning rule, so this
+ * one is the library's): n_rounds rounds of moves_per_round HMC moves
+ * (real moves of the chain, advancing its iteration counter), after each a
+ * Robbins-Monro step on ln eps_max toward the acceptance rate `target`
+ * (0 < target < 1) with gain 2 / sqrt(round), at most a factor 2 per round.
+ * The adapted eps_max replaces the configured one from then on;
+ * eps_max_out (host, may be NULL) receives it.  Single-chain contexts. */
+bps_status bps_adapt_step_size(bps_ctx* ctx, int n_rounds, int moves_per_round, double target,
+                               double* eps_max_out);
 
 /* Power-spectrum draw (Sec. 4.2): sigma_m = (V_cell/N^3) sum_{k in m} |delta_k|^2
  * over the full grid, x_m ~ chi^2 with beta_m = n_m + 2 alpha - 2 degrees of
@@ -232,6 +245,12 @@ typedef struct bps_mlp bps_mlp;
 bps_status bps_set_mass_net(bps_ctx* ctx, const bps_mlp* net, const float* feat_mean, const float* feat_std,
                             double log_clamp);
 
+/* Install a trained preconditioner saved with bps_mlp_export (the library's
+ * own format: the network, its feature standardisation and the clamp) as the
+ * network mass of ctx, exactly as bps_set_mass_net with those arguments.
+ * BPS_EINVAL if blob (host, `bytes` long) is not in that format. */
+bps_status bps_set_preconditioner(bps_ctx* ctx, const void* blob, size_t bytes);
+
 /* The mass multipliers in use by chain `chain` (0 for a single context):
  * *n_mass_bins receives their number, scales (host double [64]) the values. */
 bps_status bps_get_mass_scale(bps_ctx* ctx, int chain, int* n_mass_bins, double* scales);
@@ -263,6 +282,12 @@ bps_status bps_mlp_adam_step(bps_mlp* net, float lr);
  * be NULL) receives the loss of the last minibatch. */
 bps_status bps_mlp_train(bps_mlp* net, int n_examples, const float* x_dev, const float* t_dev, int batch,
                          int steps, float lr, uint64_t seed, double* last_loss);
+/* Save net with its feature standardisation (host float [input width] each) and
+ * log_clamp in the library format for bps_set_preconditioner.  blob NULL:
+ * *bytes receives the size needed; else *bytes is the capacity of blob (host)
+ * and receives the size written. */
+bps_status bps_mlp_export(bps_mlp* net, const float* feat_mean, const float* feat_std, double log_clamp, void* blob,
+                          size_t* bytes);
 void bps_mlp_destroy(bps_mlp* net);
 
 /* ---- building blocks of the path, for verification ---- */

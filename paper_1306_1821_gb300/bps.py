@@ -45,6 +45,9 @@ _SIGS = {
     "bps_set_data_host": ([_P, _P, _P], ctypes.c_int),
     "bps_set_data_host_u16": ([_P, _P, _P], ctypes.c_int),
     "bps_z_line_pairs": ([_P], ctypes.c_int),
+    "bps_adapt_step_size": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D], ctypes.c_int),
+    "bps_set_preconditioner": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
+    "bps_mlp_export": ([_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "bps_set_state": ([_P, _P, _D, _D, _D, ctypes.c_uint64], ctypes.c_int),
     "bps_get_state": ([_P, _P, _D, _D, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "bps_get_spectrum": ([_P, _P], ctypes.c_int),
@@ -207,6 +210,13 @@ def bps_hmc_step(ctx, want_info=True):
     info = bps_move_info()
     _check(ctx, load().bps_hmc_step(ctx, ctypes.byref(info) if want_info else None))
     return (info.accepted, info.dH, info.eps) if want_info else None
+
+
+def bps_adapt_step_size(ctx, n_rounds, moves_per_round, target):
+    out = np.zeros(1)
+    _check(ctx, load().bps_adapt_step_size(ctx, int(n_rounds), int(moves_per_round), float(target),
+                                           out.ctypes.data_as(_D)))
+    return float(out[0])
 
 
 def bps_sample_power(ctx, n_bins, want=True):
@@ -422,6 +432,24 @@ def bps_set_mass_net(ctx, net, feat_mean=None, feat_std=None, log_clamp=None):
     sd = np.ascontiguousarray(feat_std, dtype=np.float32)
     _check(ctx, load().bps_set_mass_net(ctx, net.ptr, mu.ctypes.data_as(_P), sd.ctypes.data_as(_P),
                                         float(log_clamp)))
+
+
+def bps_mlp_export(net, feat_mean, feat_std, log_clamp):
+    """The library-format bytes of a trained preconditioner."""
+    mu = np.ascontiguousarray(feat_mean, dtype=np.float32)
+    sd = np.ascontiguousarray(feat_std, dtype=np.float32)
+    n = ctypes.c_size_t(0)
+    _check(None, load().bps_mlp_export(net.ptr, mu.ctypes.data_as(_P), sd.ctypes.data_as(_P), float(log_clamp), None,
+                                       ctypes.byref(n)))
+    buf = (ctypes.c_ubyte * n.value)()
+    _check(None, load().bps_mlp_export(net.ptr, mu.ctypes.data_as(_P), sd.ctypes.data_as(_P), float(log_clamp), buf,
+                                       ctypes.byref(n)))
+    return bytes(buf)
+
+
+def bps_set_preconditioner(ctx, blob):
+    buf = (ctypes.c_ubyte * len(blob)).from_buffer_copy(blob)
+    _check(ctx, load().bps_set_preconditioner(ctx, buf, len(blob)))
 
 
 def bps_get_mass_scale(ctx, chain=0):

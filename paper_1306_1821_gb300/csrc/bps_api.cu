@@ -1222,6 +1222,39 @@ bps_status bps_hmc_step(bps_ctx* ctx, bps_move_info* info) {
   return BPS_OK;
 }
 
+bps_status bps_adapt_step_size(bps_ctx* ctx, int n_rounds, int moves_per_round, double target,
+                               double* eps_max_out) {
+  bps_status st = need_data(ctx);
+  if (st != BPS_OK) return st;
+  if (n_rounds < 1 || moves_per_round < 1 || !(target > 0.0 && target < 1.0))
+    return fail(ctx, BPS_EINVAL, "need n_rounds >= 1, moves_per_round >= 1 and 0 < target < 1");
+  unsigned long long m0 = 0, a0 = 0;
+  st = ds_read_bytes(ctx, 0, DS_OFF(n_moves), &m0, sizeof(m0));
+  if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(n_accepted), &a0, sizeof(a0));
+  if (st != BPS_OK) return st;
+  for (int r = 0; r < n_rounds; ++r) {
+    for (int i = 0; i < moves_per_round; ++i) {
+      st = hmc_move(ctx, true);
+      if (st != BPS_OK) return st;
+    }
+    unsigned long long m1 = 0, a1 = 0;
+    st = ds_read_bytes(ctx, 0, DS_OFF(n_moves), &m1, sizeof(m1));
+    if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(n_accepted), &a1, sizeof(a1));
+    if (st == BPS_OK) st = check_status(ctx);
+    if (st != BPS_OK) return st;
+    const double acc = m1 > m0 ? (double)(a1 - a0) / (double)(m1 - m0) : target;
+    m0 = m1;
+    a0 = a1;
+    // Robbins-Monro step on ln eps_max with a decreasing gain, at most a factor 2 per round
+    const double gain = 2.0 / std::sqrt((double)(r + 1));
+    const double step = std::max(-std::log(2.0), std::min(std::log(2.0), gain * (acc - target)));
+    ctx->cfg.eps_max *= std::exp(step);
+  }
+  drop_graph(ctx);   // eps_max is a launch argument of the captured iteration
+  if (eps_max_out) *eps_max_out = ctx->cfg.eps_max;
+  return BPS_OK;
+}
+
 bps_status bps_sample_power(bps_ctx* ctx, double* P_out, double* sigma_out) {
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
@@ -1366,6 +1399,53 @@ bps_status bps_set_mass_net(bps_ctx* ctx, const bps_mlp* net, const float* feat_
     g->n_mass = n_out;
   }
   return BPS_OK;
+}
+
+// Library format of a trained preconditioner (bps_mlp_export): "BPSM", version
+// 1, n_layers, widths[n_layers + 1] (uint32 each), log_clamp (double), feature
+// means and standard deviations (float [width 0] each), parameters (float,
+// layout of bps_mlp_set_params); host byte order.
+bps_status bps_set_preconditioner(bps_ctx* ctx, const void* blob, size_t bytes) {
+  if (!ctx || !blob) return fail(ctx, BPS_EINVAL, "null argument");
+  const unsigned char* b = static_cast<const unsigned char*>(blob);
+  auto rd32 = [&](size_t off) {
+    uint32_t v;
+    std::memcpy(&v, b + off, 4);
+    return v;
+  };
+  if (bytes < 12 || std::memcmp(b, "BPSM", 4) != 0 || rd32(4) != 1u)
+    return fail(ctx, BPS_EINVAL, "not a preconditioner in the library format");
+  const uint32_t L = rd32(8);
+  if (L < 1 || L > 4) return fail(ctx, BPS_EINVAL, "preconditioner: 1..4 layers");
+  size_t off = 12;
+  if (bytes < off + 4 * (L + 1) + 8) return fail(ctx, BPS_EINVAL, "preconditioner: truncated");
+  int sizes[5];
+  for (uint32_t l = 0; l <= L; ++l) sizes[l] = (int)rd32(off + 4 * l);
+  off += 4 * (L + 1);
+  double clamp;
+  std::memcpy(&clamp, b + off, 8);
+  off += 8;
+  size_t n_params = 0;
+  for (uint32_t l = 0; l < L; ++l) {
+    if (sizes[l] < 1 || sizes[l] > 512 || sizes[l + 1] < 1 || sizes[l + 1] > 512)
+      return fail(ctx, BPS_EINVAL, "preconditioner: layer widths must be in 1..512");
+    n_params += (size_t)sizes[l] * sizes[l + 1] + sizes[l + 1];
+  }
+  const size_t need = off + 2 * 4 * (size_t)sizes[0] + 4 * n_params;
+  if (bytes != need) return fail(ctx, BPS_EINVAL, "preconditioner: size does not match its layout");
+  std::vector<float> mean(sizes[0]), sd(sizes[0]), params(n_params);
+  std::memcpy(mean.data(), b + off, 4 * (size_t)sizes[0]);
+  off += 4 * (size_t)sizes[0];
+  std::memcpy(sd.data(), b + off, 4 * (size_t)sizes[0]);
+  off += 4 * (size_t)sizes[0];
+  std::memcpy(params.data(), b + off, 4 * n_params);
+  bps_mlp* net = nullptr;
+  bps_status st = bps_mlp_create((int)L, sizes, ctx->is_batch ? ctx->groups[0]->stream : ctx->stream, &net);
+  if (st != BPS_OK) return fail(ctx, st, "preconditioner: network allocation failed");
+  st = bps_mlp_set_params(net, params.data());
+  if (st == BPS_OK) st = bps_set_mass_net(ctx, net, mean.data(), sd.data(), clamp);
+  bps_mlp_destroy(net);   // the context keeps its own copy
+  return st;
 }
 
 bps_status bps_get_mass_scale(bps_ctx* ctx, int chain, int* n_mass_bins, double* scales) {

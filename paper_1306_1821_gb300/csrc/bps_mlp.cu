@@ -434,6 +434,41 @@ bps_status bps_mlp_adam_step(bps_mlp* net, float lr) {
   return BPS_OK;
 }
 
+bps_status bps_mlp_export(bps_mlp* net, const float* feat_mean, const float* feat_std, double log_clamp, void* blob,
+                          size_t* bytes) {
+  if (!net || !bytes) return mfail(net, BPS_EINVAL, "null argument");
+  const size_t need = 12 + 4 * (size_t)(net->L + 1) + 8 + 2 * 4 * (size_t)net->sizes[0] + 4 * net->n_params;
+  if (!blob) {
+    *bytes = need;
+    return BPS_OK;
+  }
+  if (*bytes < need) return mfail(net, BPS_EINVAL, "buffer too small for the preconditioner");
+  if (!feat_mean || !feat_std) return mfail(net, BPS_EINVAL, "null argument");
+  unsigned char* b = static_cast<unsigned char*>(blob);
+  size_t off = 0;
+  auto put = [&](const void* src, size_t n) {
+    std::memcpy(b + off, src, n);
+    off += n;
+  };
+  const uint32_t version = 1, L = (uint32_t)net->L;
+  put("BPSM", 4);
+  put(&version, 4);
+  put(&L, 4);
+  for (int l = 0; l <= net->L; ++l) {
+    const uint32_t w = (uint32_t)net->sizes[l];
+    put(&w, 4);
+  }
+  put(&log_clamp, 8);
+  put(feat_mean, 4 * (size_t)net->sizes[0]);
+  put(feat_std, 4 * (size_t)net->sizes[0]);
+  std::vector<float> p(net->n_params);
+  bps_status st = bps_mlp_get_params(net, p.data());
+  if (st != BPS_OK) return st;
+  put(p.data(), 4 * net->n_params);
+  *bytes = need;
+  return BPS_OK;
+}
+
 bps_status bps_mlp_train(bps_mlp* net, int n_examples, const float* x_dev, const float* t_dev, int batch, int steps,
                          float lr, uint64_t seed, double* last_loss) {
   if (!net || !x_dev || !t_dev || n_examples < 1 || batch < 1 || steps < 0)

@@ -136,5 +136,19 @@ class Preconditioner:
         """Make the network the per-move mass of a context (single or batch)."""
         bps.bps_set_mass_net(ctx, self.net, self.mu, self.sd, LOG_CLAMP)
 
+    def export(self):
+        """The library-format bytes (network, standardisation, clamp) for bps_set_preconditioner."""
+        return bps.bps_mlp_export(self.net, self.mu, self.sd, LOG_CLAMP)
+
+    def save(self, path):
+        with open(path, "wb") as f:
+            f.write(self.export())
+
     def close(self):
         self.net.close()
+
+
+def install_saved(ctx, path):
+    """Install a preconditioner saved by Preconditioner.save on a context."""
+    with open(path, "rb") as f:
+        bps.bps_set_preconditioner(ctx, f.read())

@@ -305,3 +305,23 @@ def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
         assert bps.bps_z_line_pairs(s.ctx) == 8
     finally:
         s.close()
+
+
+def test_step_size_adaptation_moves_acceptance_toward_target(torch_cuda):
+    from paper_1306_1821_gb300 import bps
+    pb = Problem(16, n_sub=1, n_bins=4, n_leapfrog=6, eps_max=0.8)      # far too large a step
+    s = pb.gpu(seed=5)
+    try:
+        def rate(n=40):
+            acc = sum(bps.bps_hmc_step(s.ctx)[0] for _ in range(n))
+            return acc / n
+        before = rate()
+        eps = bps.bps_adapt_step_size(s.ctx, 12, 20, 0.8)
+        after = rate()
+        assert eps < 0.8
+        assert after > before
+        assert abs(after - 0.8) < 0.2, (before, after, eps)
+        with pytest.raises(bps.BpsError):
+            bps.bps_adapt_step_size(s.ctx, 1, 1, 1.5)
+    finally:
+        s.close()

@@ -231,3 +231,28 @@ def test_invalid_preconditioner_arguments_are_rejected():
         bps.MLP([8, 0, 5])
     with pytest.raises(bps.BpsError):
         bps.MLP([8, 8, 8, 8, 8, 8])                            # more than four layers
+
+
+def test_saved_preconditioner_installs_identically(tmp_path):
+    from paper_1306_1821_gb300 import bps, precond
+    pb = Problem(16, n_sub=1, n_bins=4, n_leapfrog=6, eps_max=0.2)
+    net, p32, mu, sd = random_net(8, 5, 17)
+    a = sampler(pb, 7, 0)
+    b = sampler(pb, 7, 0)
+    try:
+        bps.bps_set_mass_net(a.ctx, net, mu, sd, np.log(16.0))
+        blob = bps.bps_mlp_export(net, mu, sd, np.log(16.0))
+        path = tmp_path / "mass.bpsm"
+        path.write_bytes(blob)
+        precond.install_saved(b.ctx, str(path))
+        for _ in range(2):
+            assert bps.bps_hmc_step(a.ctx) == bps.bps_hmc_step(b.ctx)
+        assert np.array_equal(bps.bps_get_mass_scale(a.ctx), bps.bps_get_mass_scale(b.ctx))
+        with pytest.raises(bps.BpsError):
+            bps.bps_set_preconditioner(b.ctx, blob[:-4])
+        with pytest.raises(bps.BpsError):
+            bps.bps_set_preconditioner(b.ctx, b"XXXX" + blob[4:])
+    finally:
+        net.close()
+        a.close()
+        b.close()
