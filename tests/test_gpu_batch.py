@@ -97,3 +97,44 @@ def test_batch_chain_equals_single_context():
             s.close()
     finally:
         bps.bps_destroy(batch)
+
+
+def test_batch_with_network_mass_equals_single_contexts():
+    import torch
+
+    from oracle import mlp
+    from paper_1306_1821_gb300 import bps
+    ps = problems()
+    sizes = [6, 16, 16, 4]                       # 2 n_bins inputs (3 bins), 4 mass bins
+    net = bps.MLP(sizes)
+    rng = np.random.default_rng(3)
+    params = mlp.init_params(sizes, 4)
+    for i in range(1, len(params), 2):
+        params[i] = rng.standard_normal(params[i].shape) * 0.1
+    net.set_params(bps.flatten_params(params))
+    mu, sd = rng.standard_normal(6), rng.uniform(0.5, 2.0, 6)
+    cfg = config(bps, 70)
+    batch = bps.bps_create_batch(SIZES, [p[0].box for p in ps], NSUB, cfg)
+    try:
+        for j, (wl, counts, R, d32) in enumerate(ps):
+            P, b, nbar = inputs.initial_state(wl)
+            bps.bps_batch_set_chain(batch, j, torch.from_numpy(counts).cuda(), torch.from_numpy(R).cuda(),
+                                    torch.from_numpy(d32).cuda(), P, b, nbar, 0)
+        bps.bps_set_mass_net(batch, net, mu, sd, np.log(16.0))
+        rec = bps.bps_batch_gibbs_iterate(batch, 2, len(ps))
+        for j in (0, 3):
+            wl, counts, R, d32 = ps[j]
+            P, b, nbar = inputs.initial_state(wl)
+            s = bps.Sampler(wl.N, wl.box, wl.n_sub, 3, n_leapfrog=5, eps_max=0.25, jump=1, jump_leapfrog=3,
+                            jump_eps_max=0.2, fixed_bias_index=0, seed=70 + j)
+            bps.bps_set_data(s.ctx, torch.from_numpy(counts).cuda(), torch.from_numpy(R).cuda())
+            bps.bps_set_state(s.ctx, torch.from_numpy(d32).cuda(), P, b, nbar, 0)
+            bps.bps_set_mass_net(s.ctx, net, mu, sd, np.log(16.0))
+            single = bps.bps_gibbs_iterate(s.ctx, 2, s.rec_len)
+            slot = bps.bps_batch_record_slot(batch, j)
+            assert np.allclose(rec[:, slot, :s.rec_len], single, rtol=1e-5, atol=1e-6)
+            assert np.allclose(bps.bps_get_mass_scale(batch, j), bps.bps_get_mass_scale(s.ctx), rtol=1e-6)
+            s.close()
+    finally:
+        bps.bps_destroy(batch)
+        net.close()
