@@ -286,17 +286,27 @@ def test_host_upload_equals_device_upload(torch_cuda):
 
 
 def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
+    # in a fresh process (the choice is cached per process): a new kind of
+    # context times the tile sizes, keeps one and writes it to the cache file
+    import json
+    import os
+    import subprocess
+    import sys
+
     from paper_1306_1821_gb300 import bps
     path = tmp_path / "tune.json"
-    monkeypatch.setenv("BPS_TUNE_CACHE", str(path))
-    cfg = bps.make_config(2, n_leapfrog=2, eps_max=0.1)
-    batch = bps.bps_create_batch([8, 8, 8], [100.0, 100.0, 100.0], [1, 1, 1], cfg)   # a kind no other test makes
-    try:
-        lp = bps.bps_z_line_pairs(batch)
-        assert lp in (4, 8, 16)
-    finally:
-        bps.bps_destroy(batch)
-    import json
+    code = ("from paper_1306_1821_gb300 import bps\n"
+            "cfg = bps.make_config(2, n_leapfrog=2, eps_max=0.1)\n"
+            "b = bps.bps_create_batch([8, 8, 8], [100.0] * 3, [1, 1, 1], cfg)\n"
+            "print(bps.bps_z_line_pairs(b))\n"
+            "bps.bps_destroy(b)\n")
+    env = dict(os.environ, BPS_TUNE_CACHE=str(path))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lp = int(out.stdout.strip().splitlines()[-1])
+    assert lp in (4, 8, 16)
     cache = json.loads(path.read_text())
     assert any(k.endswith("N=8 chains=3 zpairs") and v == lp for k, v in cache.items())
     monkeypatch.setenv("BPS_AUTOTUNE", "0")
