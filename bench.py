@@ -499,6 +499,7 @@ def pk_ess(rec, n_bins, N, secs):
             "sd_lnP": [round(float(v), 4) for v in np.log(P).std(0)]}
 
 
+DAMPED = 0.6          # damping of the second network arm (it learns 0.6 ln s)
 PRECOND_RUNS = {
     # workload: (survey, training surveys, mass bins)
     "precond128": ("survey128", 64, 64),
@@ -533,6 +534,8 @@ def run_precond(args):
     F2, T2 = precond.measure(probs, n_mass, n_moves=300, burn_in=100, sampler_mass=pc)
     pc2 = precond.Preconditioner(F.shape[1], n_mass, seed=1)
     loss = pc2.fit(F2, T2, steps=2000, batch=64)
+    pc3 = precond.Preconditioner(F.shape[1], n_mass, seed=1)
+    pc3.fit(F2, T2, steps=2000, batch=64, damping=DAMPED)
     train_s = time.time() - t0
     delta, counts, R = inputs.make_survey(wl)
     P0, b0, n0 = inputs.initial_state(wl)
@@ -540,13 +543,15 @@ def run_precond(args):
     Rt = torch.from_numpy(R).cuda()
     d32 = torch.from_numpy(delta.astype(np.float32)).cuda()
     arms = {}
-    for arm in ("plain", "network"):
+    for arm in ("plain", "network", "network_damped"):
         s = bps.Sampler(wl.N, wl.box, wl.n_sub, wl.n_bins, n_leapfrog=wl.n_leapfrog, eps_max=wl.eps_max, jump=1,
                         jump_leapfrog=10, jump_eps_max=jeps, fixed_bias_index=0, seed=3)
         bps.bps_set_data(s.ctx, cnt, Rt)
         bps.bps_set_state(s.ctx, d32, P0, b0, n0, 0)
         if arm == "network":
             pc2.install(s.ctx)
+        elif arm == "network_damped":
+            pc3.install(s.ctx)
         bps.bps_gibbs_iterate(s.ctx, max(args.warmup, 300))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -559,7 +564,7 @@ def run_precond(args):
         r = pk_ess(rec, wl.n_bins, wl.N, secs)
         r["hmc_acceptance"] = float(np.mean(rec[:, -1]))
         r["ms_per_iteration"] = 1000.0 * secs / args.ess_iters
-        if arm == "network":
+        if arm != "plain":
             r["mass_scales_in_use"] = [round(float(v), 3) for v in bps.bps_get_mass_scale(s.ctx)]
         s.close()
         arms[arm] = r
@@ -576,14 +581,19 @@ def run_precond(args):
                                f"{wl.n_leapfrog} leapfrog steps (eps_max {wl.eps_max}), jump on (10 steps, "
                                f"eps_max {jeps}); network {2 * wl.n_bins}-128-128-{n_mass} trained on {n_train} "
                                "random surveys of the same recipe, the survey itself held out"},
-        "plain": arms["plain"], "network": arms["network"],
+        "plain": arms["plain"], "network": arms["network"], "network_damped": arms["network_damped"],
+        "damping_of_network_damped": DAMPED,
         "ratio_min_ess_per_s": arms["network"]["min_ess_per_s"] / arms["plain"]["min_ess_per_s"],
         "ratio_median_ess_per_s": arms["network"]["median_ess_per_s"] / arms["plain"]["median_ess_per_s"],
+        "ratio_damped_min_ess_per_s": arms["network_damped"]["min_ess_per_s"] / arms["plain"]["min_ess_per_s"],
+        "ratio_damped_median_ess_per_s": (arms["network_damped"]["median_ess_per_s"]
+                                          / arms["plain"]["median_ess_per_s"]),
         "training": {"seconds": train_s, "examples": int(2 * len(F)), "final_minibatch_loss": loss},
     }
     print(json.dumps(line), flush=True)
     pc.close()
     pc2.close()
+    pc3.close()
     return 0
 
 

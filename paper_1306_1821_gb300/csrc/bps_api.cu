@@ -1012,7 +1012,6 @@ bps_status mass_stats(bps_ctx* ctx, int n_moves, int n_mass, double* out, int ou
     if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(mstat), zero.data(), MAXB * sizeof(double));
     if (st != BPS_OK) return st;
   }
-  const int keep_mass = ctx->n_mass;
   ctx->n_mass = n_mass;   // the mass-bin table now has n_mass bins
   drop_graph(ctx);
   Fields f = fields(ctx);
@@ -1028,7 +1027,6 @@ bps_status mass_stats(bps_ctx* ctx, int n_moves, int n_mass, double* out, int ou
   launch_mstat(sa, region_offset(ctx, RG_BIN), ctx->pt.x_tiles, n_mass, 1, B, s);
   LAUNCHED(ctx, 2);
   CK(cudaStreamSynchronize(s));
-  (void)keep_mass;
   // mode counts per (power bin, mass bin), full-grid weights
   const int nb = ctx->cfg.n_bins, N = ctx->N, H = N / 2;
   std::vector<double> cnt((size_t)nb * n_mass, 0.0), nj(n_mass, 0.0);
@@ -1099,7 +1097,7 @@ void bps::set_last_error(const char* msg) { g_err = msg; }
 // =================================================================== C ABI
 extern "C" {
 
-const char* bps_version(void) { return "bps 0.2 (sm_103a)"; }
+const char* bps_version(void) { return "bps 0.3 (sm_103a)"; }
 
 const char* bps_last_error(const bps_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 

@@ -112,13 +112,16 @@ class Preconditioner:
         self.sd = np.ones(n_in)
         self.net.set_params(bps.flatten_params(he_init(self.sizes, seed)))
 
-    def fit(self, feats, targ, steps=3000, batch=64, lr=2e-3, seed=1):
-        """Adam on minibatches drawn on the device; returns the last minibatch loss."""
+    def fit(self, feats, targ, steps=3000, batch=64, lr=2e-3, seed=1, damping=1.0):
+        """Adam on minibatches drawn on the device; returns the last minibatch loss.
+        damping (gamma): the network learns gamma * ln s, i.e. M -> s^gamma M.  gamma = 1
+        brings each bin's mass to the measured posterior precision (largest gain on the
+        slowest bins); smaller gamma stops short of it and costs the fast directions less."""
         import torch
         self.mu = feats.mean(0)
         self.sd = feats.std(0) + 1e-3
         x = torch.from_numpy(self.standardise(feats)).cuda()
-        t = torch.from_numpy(targ.astype(np.float32)).cuda()
+        t = torch.from_numpy((damping * targ).astype(np.float32)).cuda()
         return self.net.train(x, t, batch=batch, steps=steps, lr=lr, seed=seed)
 
     def standardise(self, feats):
