@@ -64,6 +64,7 @@ struct bps_ctx {
   void (*zgrad)(const Fields&, int region, int nch, cudaStream_t) = nullptr;
   int zgrad_tiles = 0;
   int zgrad_pairs = 8;
+  YzEntry yz{};                 // fused y^-1 / z / y stage (run == nullptr: three passes)
   MassNet* mnet = nullptr;      // network mass (bps_set_mass_net): scales recomputed before every move
   std::vector<char> have_data;
   int rebuild_blocks = 0;
@@ -318,6 +319,36 @@ bps_status rebuild_all(bps_ctx* ctx) {
   return BPS_OK;
 }
 
+// Likelihood-energy partials written by one force stage.
+int lik_tiles(const bps_ctx* ctx) { return ctx->yz.run ? ctx->yz.tiles : ctx->zgrad_tiles; }
+
+// The y^-1 / z / y stage of one force evaluation (C2R, local force
+// g = a delta - c and its energy partials into `region` when >= 0, R2C): the
+// fused plane kernel where the grid has one, else the three passes.
+// Profiling kind 2 times the fused kernel; kinds 1 and 3 the y passes.
+bps_status force_stage(bps_ctx* ctx, const Fields& f, int region, bool prof, cudaStream_t s) {
+  const PassTable& P = ctx->pt;
+  const int B = ctx->batch;
+  if (ctx->yz.run) {
+    if (prof) prof_mark(ctx, 2);
+    ctx->yz.run(f, region, B, s);
+    if (prof) prof_mark(ctx, 2);
+    LAUNCHED(ctx, 1);
+    return BPS_OK;
+  }
+  if (prof) prof_mark(ctx, 1);
+  P.y_inv(f, BUF_W, B, s);
+  if (prof) prof_mark(ctx, 1);
+  if (prof) prof_mark(ctx, 2);
+  ctx->zgrad(f, region, B, s);
+  if (prof) prof_mark(ctx, 2);
+  if (prof) prof_mark(ctx, 3);
+  P.y_fwd(f, BUF_W, B, s);
+  if (prof) prof_mark(ctx, 3);
+  LAUNCHED(ctx, 3);
+  return BPS_OK;
+}
+
 bps_status hmc_move(bps_ctx* ctx, bool advance) {
   Fields f = fields(ctx);
   ScalarArgs sa = scalars(ctx);
@@ -329,27 +360,19 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   P.z_noise(f, B, s);
   P.y_fwd(f, BUF_PH, B, s);
   P.x_init(f, region_offset(ctx, RG_INIT), B, s);
-  P.y_inv(f, BUF_W, B, s);
-  ctx->zgrad(f, region_offset(ctx, RG_LIK0), B, s);
-  P.y_fwd(f, BUF_W, B, s);
+  bps_status sf = force_stage(ctx, f, region_offset(ctx, RG_LIK0), false, s);
+  if (sf != BPS_OK) return sf;
   for (int st = 1; st <= L; ++st) {
     prof_mark(ctx, 0);
     P.x_leap(f, st == 1 ? 1 : 0, B, s);
     prof_mark(ctx, 0);
-    prof_mark(ctx, 1);
-    P.y_inv(f, BUF_W, B, s);
-    prof_mark(ctx, 1);
-    prof_mark(ctx, 2);
-    ctx->zgrad(f, st == L ? region_offset(ctx, RG_LIK1) : -1, B, s);
-    prof_mark(ctx, 2);
-    prof_mark(ctx, 3);
-    P.y_fwd(f, BUF_W, B, s);
-    prof_mark(ctx, 3);
+    sf = force_stage(ctx, f, st == L ? region_offset(ctx, RG_LIK1) : -1, true, s);
+    if (sf != BPS_OK) return sf;
   }
   P.x_final(f, region_offset(ctx, RG_FINAL), B, s);
   launch_move_end(sa, region_offset(ctx, RG_INIT), region_offset(ctx, RG_LIK0), region_offset(ctx, RG_FINAL),
-                  region_offset(ctx, RG_LIK1), P.x_tiles, ctx->zgrad_tiles, B, s);
-  int n = 9 + 4 * L + (ctx->mnet ? 1 : 0);
+                  region_offset(ctx, RG_LIK1), P.x_tiles, lik_tiles(ctx), B, s);
+  int n = 6 + L + (ctx->mnet ? 1 : 0);
   if (advance) {
     launch_advance(ctx->ds, B, s);
     ++n;
@@ -401,13 +424,12 @@ bps_status jump_gradient(bps_ctx* ctx) {
   const PassTable& P = ctx->pt;
   const int B = ctx->batch;
   P.x_jinv(f, B, s);
-  P.y_inv(f, BUF_W, B, s);
-  ctx->zgrad(f, region_offset(ctx, RG_JLIK), B, s);
-  P.y_fwd(f, BUF_W, B, s);
+  bps_status sf = force_stage(ctx, f, region_offset(ctx, RG_JLIK), false, s);
+  if (sf != BPS_OK) return sf;
   P.x_jgrad(f, region_offset(ctx, RG_JGRAD), B, s);
-  launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), ctx->zgrad_tiles, B,
+  launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), lik_tiles(ctx), B,
                      s);
-  LAUNCHED(ctx, 6);
+  LAUNCHED(ctx, 3);
   return BPS_OK;
 }
 
@@ -707,7 +729,13 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
   ctx->n_sm = sms > 0 ? sms : 148;
   // the voxel kernels of a batch run B chains side by side: fewer blocks each
   ctx->rebuild_blocks = std::max(1, std::min(4 * ctx->n_sm / B + 1, (int)(ctx->nv / 1024) + 1));
+  // fused y^-1 / z / y stage where the grid has one; BPS_FUSED_YZ=0 keeps the three passes
+  {
+    const char* e = std::getenv("BPS_FUSED_YZ");
+    if (!(e && std::atoi(e) == 0) && !yz_table(grid_n, &ctx->yz)) ctx->yz = YzEntry{};
+  }
   ctx->part_stride = std::max(std::max(std::max(pt.x_tiles, pt.z_tiles), pt.z_lp_tiles[0]), ctx->rebuild_blocks);
+  ctx->part_stride = std::max(ctx->part_stride, ctx->yz.tiles);
   ctx->part_cstride = (long long)region_total() * ctx->part_stride;
 
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
@@ -1496,14 +1524,13 @@ bps_status bps_gradient(bps_ctx* ctx, float* grad_dev, double* energies) {
   cudaStream_t s = ctx->stream;
   launch_move_begin(sa, 1, s);   // per-bin tables of the current P and abar
   ctx->pt.x_inv(f, -1, ctx->W, 1, s);
-  ctx->pt.y_inv(f, BUF_W, 1, s);
-  ctx->zgrad(f, region_offset(ctx, RG_LIK0), 1, s);
-  ctx->pt.y_fwd(f, BUF_W, 1, s);
+  bps_status sf = force_stage(ctx, f, region_offset(ctx, RG_LIK0), false, s);
+  if (sf != BPS_OK) return sf;
   ctx->pt.x_grad(f, ctx->W, region_offset(ctx, RG_GRAD), 1, s);
   double* scratch = reinterpret_cast<double*>(ds_addr(ctx, 0, DS_OFF(scratch)));
   launch_reduce_to(sa, region_offset(ctx, RG_GRAD), ctx->pt.x_tiles, 1, 0.5 / (double)ctx->nv, scratch, s);
-  launch_reduce_to(sa, region_offset(ctx, RG_LIK0), ctx->zgrad_tiles, 1, 1.0, scratch + 1, s);
-  LAUNCHED(ctx, 8);
+  launch_reduce_to(sa, region_offset(ctx, RG_LIK0), lik_tiles(ctx), 1, 1.0, scratch + 1, s);
+  LAUNCHED(ctx, 5);
   st = copy_spec_out(ctx, ctx->W, grad_dev);
   if (st != BPS_OK) return st;
   if (energies) {

@@ -43,6 +43,16 @@ struct PassTable {
 };
 
 bool pass_table(int N, PassTable* out);
+
+// The fused y^-1 / z / y stage of a force evaluation (bps_yz.cu): one CTA per
+// x plane holds the plane in shared memory, so W is read and written once.
+// `tiles` is the number of likelihood-energy partials it writes (one per CTA).
+// Grids without a fused kernel keep the three passes.
+struct YzEntry {
+  void (*run)(const Fields&, int region, int nch, cudaStream_t) = nullptr;
+  int tiles = 0;
+};
+bool yz_table(int N, YzEntry* out);
 void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int nch, cudaStream_t s);
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
                  int stride, int blocks, cudaStream_t s);
