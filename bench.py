@@ -137,6 +137,27 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def z_pass_bytes(R, N):
+    """Algorithmic bytes of one force z pass on this survey.  a and c vanish
+    outside the voxels with R > 0, so the pass needs: W read on the z lines that
+    meet the survey, W written on every line, and a and c over each line's
+    support [lo, hi) (its first and last observed voxel, widened to multiples of
+    four floats for 16-byte copies)."""
+    import numpy as np
+    obs = (np.asarray(R) > 0).any(axis=0).reshape(N * N, N)
+    has = obs.any(axis=1)
+    first = np.argmax(obs, axis=1)
+    last = N - 1 - np.argmax(obs[:, ::-1], axis=1)
+    lo = first & ~3
+    hi = (last + 4) & ~3
+    span = np.where(has, hi - lo, 0).astype(np.int64)
+    row = (N // 2 + 1) * 8
+    total = row * (int(has.sum()) + N * N) + 2 * 4 * int(span.sum())
+    info = {"lines_with_support": float(has.mean()), "support_voxels": float(span.sum()) / N ** 3,
+            "dense_bytes": 2 * row * N * N + 2 * 4 * N ** 3}
+    return total, info
+
+
 def read_traffic():
     """DRAM bytes per x-pass launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
@@ -347,15 +368,15 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (the x pass), from the live events
     S_c = wl.N * wl.N * (wl.N // 2 + 1) * 8
-    S_r = wl.N ** 3 * 4
-    bytes_kind = [6 * S_c, 2 * S_c, 2 * S_c + 2 * S_r, 2 * S_c]
+    z_bytes, z_info = z_pass_bytes(R, wl.N)
+    bytes_kind = [6 * S_c, 2 * S_c, z_bytes, 2 * S_c]
     per_launch_ms = [kms[i] / max(kn[i], 1) for i in range(4)]
     shares = [kms[i] / max(sum(kms), 1e-30) for i in range(4)]
     peak, peak_kind = measured_peaks()
     dom = int(np.argmax(kms))
     achieved = bytes_kind[dom] / (per_launch_ms[dom] * 1e-3) / 1e9
     leap_ms = sum(per_launch_ms)
-    leap_bytes = 12 * S_c + 2 * S_r
+    leap_bytes = 10 * S_c + z_bytes
     traffic = read_traffic() if dom == 0 else None
 
     if rank == 0:
@@ -382,7 +403,8 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": bytes_kind[dom], "launch_ms": per_launch_ms[dom]},
             "leapfrog_kernels": {KERNEL_NAMES[i]: {"ms": per_launch_ms[i], "timed_launches": int(kn[i]),
                                                    "share": shares[i], "bytes": bytes_kind[i],
-                                                   "GBps": bytes_kind[i] / (per_launch_ms[i] * 1e-3) / 1e9}
+                                                   "GBps": bytes_kind[i] / (per_launch_ms[i] * 1e-3) / 1e9,
+                                                   **(z_info if i == 2 else {})}
                                  for i in range(4)},
             "profiled_iterations": f"1 in {PROFILE_EVERY} (event pairs around each leapfrog kernel, launched "
                                    f"directly); the rest replay the iteration's CUDA graph",

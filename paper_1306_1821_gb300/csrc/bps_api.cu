@@ -48,6 +48,7 @@ struct bps_ctx {
   float2* acc = nullptr;      // running sum of the state (bps_mass_stats), allocated on first use
   float* a = nullptr;
   float* c = nullptr;
+  int2* span = nullptr;         // per-line support of a and c (grids with N % 32 == 0)
   uint16_t* cnt = nullptr;
   float* R = nullptr;
   float2* tw = nullptr;
@@ -151,6 +152,8 @@ Fields fields(bps_ctx* c) {
   f.c = c->c;
   f.cnt = c->cnt;
   f.R = c->R;
+  f.span = c->span;
+  f.span_stride = (long long)c->N * c->N;
   f.n_sub = c->max_sub;
   f.ds = c->ds;
   f.part = c->part;
@@ -541,6 +544,7 @@ void free_all(bps_ctx* c) {
   cudaFree(c->acc);
   cudaFree(c->a);
   cudaFree(c->c);
+  cudaFree(c->span);
   cudaFree(c->cnt);
   cudaFree(c->R);
   cudaFree(c->tw);
@@ -633,6 +637,7 @@ bps_status choose_zgrad(bps_ctx* ctx) {
     } else {
       cudaStream_t s = ctx->stream;
       Fields f = fields(ctx);
+      f.span = nullptr;   // time the dense pass: the buffers hold no survey yet
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
@@ -740,9 +745,11 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
 
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
   const size_t sb = ctx->n_spec * sizeof(float2) * B, rb = (size_t)ctx->nv * sizeof(float) * B;
+  const size_t span_bytes = (size_t)grid_n * grid_n * sizeof(int2) * B;
   const int rec_len = cfg->n_bins + 2 * max_sub + 2;
   bool ok = alloc((void**)&ctx->dh[0], sb) && alloc((void**)&ctx->dh[1], sb) && alloc((void**)&ctx->ph, sb) &&
             alloc((void**)&ctx->W, sb) && alloc((void**)&ctx->a, rb) && alloc((void**)&ctx->c, rb) &&
+            (grid_n % 32 != 0 || alloc((void**)&ctx->span, span_bytes)) &&
             alloc((void**)&ctx->tw, grid_n * sizeof(float2)) &&
             alloc((void**)&ctx->part, (size_t)ctx->part_cstride * B * sizeof(double)) &&
             alloc((void**)&ctx->ds, sizeof(DevState) * B) &&
@@ -773,6 +780,7 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->W, 0, sb, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->a, 0, rb, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->c, 0, rb, stream);
+  if (e == cudaSuccess && ctx->span) e = cudaMemsetAsync(ctx->span, 0, span_bytes, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     std::string msg = std::string("initialisation failed: ") + cudaGetErrorString(e);
@@ -827,6 +835,9 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float*
     }
   }
   const int blocks = ctx->rebuild_blocks;
+  // the data kernels widen this chain's per-line supports from empty
+  int2* span_ch = ctx->span ? ctx->span + (size_t)ch * ctx->N * ctx->N : nullptr;
+  if (span_ch) CK(cudaMemsetAsync(span_ch, 0, (size_t)ctx->N * ctx->N * sizeof(int2), s));
   // per-subsample partial sums side by side (4 quantities x blocks each), read back once
   double* part = ctx->part + ch * ctx->part_cstride;
   if ((long long)ns * 4 * blocks > ctx->part_cstride) return fail(ctx, BPS_EINVAL, "too many subsamples");
@@ -853,10 +864,10 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float*
     }
     if (c16)
       launch_data16(static_cast<const uint16_t*>(cl), rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv,
-                    ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, s);
+                    ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, span_ch, ctx->N, s);
     else
       launch_data(static_cast<const int32_t*>(cl), rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv,
-                  ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, s);
+                  ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, span_ch, ctx->N, s);
     LAUNCHED(ctx, 1);
     if (host) CK(cudaEventRecord(ctx->stage_free[l & 1], s));
   }

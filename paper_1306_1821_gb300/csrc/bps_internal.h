@@ -10,7 +10,6 @@ namespace bps {
 
 struct Fields;
 
-// Launchers of the field passes of one grid size (bps_passes.cu).
 // Launchers of the field passes of one grid size (bps_passes.cu).  The `nch`
 // argument is the number of chains of a batch (gridDim.y); a single-chain
 // operation passes fields already moved to its chain and nch = 1.
@@ -54,11 +53,13 @@ struct YzEntry {
 };
 bool yz_table(int N, YzEntry* out);
 void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int nch, cudaStream_t s);
+// Data check of one subsample; with `span` (N a multiple of 32) it also widens
+// the per-line support of R > 0 (Fields::span encoding).
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
-                 int stride, int blocks, cudaStream_t s);
+                 int stride, int blocks, int2* span, int n_grid, cudaStream_t s);
 // the same from 16-bit counts
 void launch_data16(const uint16_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
-                   int stride, int blocks, cudaStream_t s);
+                   int stride, int blocks, int2* span, int n_grid, cudaStream_t s);
 void launch_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
                          uint64_t* out, cudaStream_t s);
 void launch_voxel_normals(uint64_t seed, uint64_t it, size_t n, float* out, cudaStream_t s);

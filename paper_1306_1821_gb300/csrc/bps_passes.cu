@@ -53,6 +53,18 @@ struct ZArgs {
 };
 
 // ------------------------------------------------------------------ x pass helpers
+// Tile schedule of the strided (x and y) passes: the NYQ tiles of the kz = N/2
+// column come first.  Their accesses are one element per row (a quarter of each
+// 32-byte sector is used), so a Nyquist tile runs several times longer than a
+// regular one; scheduled last they formed a tail of a few SMs at the end of
+// every pass, scheduled first they overlap with the regular tiles.
+template <int N>
+__device__ __forceinline__ int tile_id() {
+  using C = Cfg<N>;
+  const int id = blockIdx.x;
+  return id < C::NYQ ? N * C::ZB + id : id - C::NYQ;
+}
+
 __device__ __forceinline__ const float2* buf_ptr(const Fields& fp, int b) {
   return b == BUF_D0 ? fp.dh[0] : b == BUF_D1 ? fp.dh[1] : b == BUF_PH ? fp.ph : fp.W;
 }
@@ -100,7 +112,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
   }
   __syncthreads();
 
-  const Tile<N> T = tile_x<N>(blockIdx.x);
+  const Tile<N> T = tile_x<N>(tile_id<N>());
   const int f = t % F;
   const int ja = t / F;                       // row group of the spatial (x-) layout
   const int ky = T.ky0 + f * T.dky, kz = T.kz0 + f * T.dkz;
@@ -458,7 +470,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_YPASS_MIN_BLOCKS) k_ypass(Fiel
   __shared__ float2 s_tw[N];
   __shared__ __align__(16) float2 s_ex[N * F];
   const int t = threadIdx.x;
-  const Tile<N> T = tile_y<N>(blockIdx.x);
+  const Tile<N> T = tile_y<N>(tile_id<N>());
   float2* data = const_cast<float2*>(buf_ptr(fp, buf));
   const int f = t % F, j = t / F;
   const long long colo = T.base + (long long)f * T.cs;
@@ -528,14 +540,47 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   const int t = threadIdx.x;
   DevState* ds = fp.ds;
-  const long long L0 = (long long)blockIdx.x * LINES;
+  // Lines in decreasing x: the y passes visit the x planes upwards, so the planes
+  // the z pass reads first are the ones the inverse y pass wrote last (still in
+  // L2), and the forward y pass starts on the planes the z pass wrote last.
+  const long long L0 = (long long)(gridDim.x - 1 - blockIdx.x) * LINES;
   constexpr bool STAGED = MODE != Z_NOISE;
+  // Z_GRAD: support [lo, hi) of a and c on each line of the tile (whole lines
+  // without support information).  Outside it a = c = 0, so g = 0 there: only
+  // the support is staged, and a tile without support has g = 0 on every line,
+  // hence a zero force, written without reading W.
+  __shared__ int s_lo[MODE == Z_GRAD ? LINES : 1], s_hi[MODE == Z_GRAD ? LINES : 1];
+  if constexpr (MODE == Z_GRAD) {
+    if (t < LINES) {
+      if (fp.span) {
+        const int2 sp = fp.span[L0 + t];
+        s_lo[t] = N - sp.x;
+        s_hi[t] = sp.y;
+      } else {
+        s_lo[t] = 0;
+        s_hi[t] = N;
+      }
+    }
+  }
   if constexpr (STAGED) {
     if (t == 0) {
       mbar_init(bar, 1);
       mbar_fence_init();
     }
     __syncthreads();
+    if constexpr (MODE == Z_GRAD) {
+      bool any = false;
+#pragma unroll
+      for (int l = 0; l < LINES; ++l) any |= s_hi[l] > s_lo[l];
+      if (!any) {
+        for (int i = t; i < LINES * (H + 1); i += NTZ) {
+          const int l = i / (H + 1), k = i - l * (H + 1);
+          fp.W[(L0 + l) * ZP + k] = make_float2(0.f, 0.f);
+        }
+        if (za.region >= 0 && t == 0) fp.part[za.region + blockIdx.x] = 0.0;
+        return;
+      }
+    }
     if (t == 0) {
       if constexpr (MODE == Z_R2C) {
         constexpr uint32_t RB = LINES * N * sizeof(float);
@@ -544,12 +589,24 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       } else {
         const float2* src = (MODE == Z_C2R) ? za.src : fp.W;
         constexpr uint32_t SB = LINES * ZP * sizeof(float2);
-        constexpr uint32_t AB = (uint32_t)L::AC;
-        mbar_expect_tx(bar, SB + 2 * AB);
-        bulk_load(s_buf, src + L0 * ZP, SB, bar);
         if constexpr (MODE == Z_GRAD) {
-          bulk_load(s_a, fp.a + L0 * N, AB, bar);
-          bulk_load(s_c, fp.c + L0 * N, AB, bar);
+          // supports are multiples of 4 floats: 16-byte aligned bulk copies
+          uint32_t acb = 0;
+          for (int l = 0; l < LINES; ++l)
+            if (s_hi[l] > s_lo[l]) acb += (uint32_t)(s_hi[l] - s_lo[l]) * sizeof(float);
+          mbar_expect_tx(bar, SB + 2 * acb);
+          bulk_load(s_buf, src + L0 * ZP, SB, bar);
+          for (int l = 0; l < LINES; ++l) {
+            if (s_hi[l] > s_lo[l]) {
+              const uint32_t nb = (uint32_t)(s_hi[l] - s_lo[l]) * sizeof(float);
+              const long long g0 = (L0 + l) * N + s_lo[l];
+              bulk_load(s_a + l * N + s_lo[l], fp.a + g0, nb, bar);
+              bulk_load(s_c + l * N + s_lo[l], fp.c + g0, nb, bar);
+            }
+          }
+        } else {
+          mbar_expect_tx(bar, SB);
+          bulk_load(s_buf, src + L0 * ZP, SB, bar);
         }
       }
     }
@@ -669,10 +726,13 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
     float e = 0.f;
     if (f < LP) {
       const int ra = (2 * f) * N, rb = ra + N;
+      const int loa = s_lo[2 * f], hia = s_hi[2 * f], lob = s_lo[2 * f + 1], hib = s_hi[2 * f + 1];
 #pragma unroll
       for (int d = 0; d < R2; ++d) {
         const int n = c + R1 * d;
-        const float aa = s_a[ra + n], ca = s_c[ra + n], ab = s_a[rb + n], cb = s_c[rb + n];
+        const bool ina = n >= loa && n < hia, inb = n >= lob && n < hib;
+        const float aa = ina ? s_a[ra + n] : 0.f, ca = ina ? s_c[ra + n] : 0.f;
+        const float ab = inb ? s_a[rb + n] : 0.f, cb = inb ? s_c[rb + n] : 0.f;
         const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
         const float ga = fmaf(aa, da, -ca), gb = fmaf(ab, db, -cb);
         e += da * (ga - ca) + db * (gb - cb);   // a d^2 - 2 c d
@@ -758,9 +818,15 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
 // sums R, N^2/R, #(R>0) over R > 0 and the number of invalid voxels.  Per
 // thread the sums run in FP32 with Kahan compensation and the counts in
 // integers (FP64 arithmetic is slow on this part); blocks combine in FP64.
+//
+// With `span` (grids with N a multiple of 32, so that a warp's 32 voxels lie on
+// one z line) the kernel also widens each line's support [lo, hi) to the
+// voxels with R > 0: a warp ballot, then two atomics by the warp's first lane.
+// Since counts are zero where R = 0, a and c vanish outside the union of these
+// supports over the subsamples.
 template <typename CT>
 __global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, uint16_t* cout, float* rout,
-                                              long long nv, double* part, int stride) {
+                                              long long nv, double* part, int stride, int2* span, int n_grid) {
   __shared__ double s_red[32];
   float sR = 0.f, cR = 0.f, sB = 0.f, cB = 0.f;
   unsigned int no = 0, bad = 0;
@@ -770,6 +836,17 @@ __global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, u
     const bool rok = (r >= 0.f) && isfinite(r);
     const bool nok = n >= 0 && n <= 65535;
     if (!rok || !nok || (r == 0.f && n > 0)) ++bad;
+    if (span) {
+      const unsigned m = __ballot_sync(0xffffffffu, rok && r > 0.f);
+      if (m != 0u && (threadIdx.x & 31) == 0) {
+        const long long line = i / n_grid;
+        const int z0 = (int)(i - line * n_grid);
+        const int lo = (z0 + __ffs((int)m) - 1) & ~3;
+        const int hi = (z0 + 32 - __clz((int)m) + 3) & ~3;
+        atomicMax(&span[line].x, n_grid - lo);
+        atomicMax(&span[line].y, hi);
+      }
+    }
     cout[i] = (uint16_t)(nok ? n : 0);
     rout[i] = rok ? r : 0.f;
     if (rok && r > 0.f) {
@@ -900,12 +977,12 @@ void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int 
   k_rebuild<<<dim3(blocks, nch), 256, 0, s>>>(fp, nv, region);
 }
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
-                 int stride, int blocks, cudaStream_t s) {
-  k_data<int32_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride);
+                 int stride, int blocks, int2* span, int n_grid, cudaStream_t s) {
+  k_data<int32_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
 }
 void launch_data16(const uint16_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
-                   int stride, int blocks, cudaStream_t s) {
-  k_data<uint16_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride);
+                   int stride, int blocks, int2* span, int n_grid, cudaStream_t s) {
+  k_data<uint16_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
 }
 void launch_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
                          uint64_t* out, cudaStream_t s) {

@@ -29,6 +29,10 @@ struct Fields {
   float* c;               // local drive      c = sum_l b_l (N^l - Nbar_l R^l)
   const uint16_t* cnt;    // counts [n_sub][N^3]
   const float* R;         // response [n_sub][N^3]
+  // Support of a and c along each z line (x, y): span[x N + y] = (N - lo, hi),
+  // lo and hi multiples of 4, a = c = 0 outside [lo, hi) (empty when hi <= lo).
+  // NULL: dense (no support information).
+  const int2* span;
   int n_sub;
   DevState* ds;
   double* part;           // per-block partial sums (FP64)
@@ -43,6 +47,7 @@ struct Fields {
   long long real_stride;  // voxels per real field
   long long data_stride;  // elements per chain of counts / response (max subsamples x voxels)
   long long part_cstride; // doubles of partial sums per chain
+  long long span_stride;  // lines per chain (N^2)
 };
 
 // The fields of chain `ch` of a batch (blockIdx.y of the field passes).
@@ -56,6 +61,7 @@ __host__ __device__ __forceinline__ Fields at_chain(Fields f, int ch) {
   f.c += ch * f.real_stride;
   f.cnt += ch * f.data_stride;
   f.R += ch * f.data_stride;
+  if (f.span) f.span += ch * f.span_stride;
   f.ds += ch;
   f.part += ch * f.part_cstride;
   return f;

@@ -52,7 +52,8 @@ struct YZ {
   static constexpr size_t OFF_TWN = OFF_EX + EX;
   static constexpr size_t OFF_TWM = OFF_TWN + (size_t)N * sizeof(float2);
   static constexpr size_t OFF_RED = OFF_TWM + (size_t)M * sizeof(float2);
-  static constexpr size_t OFF_BAR = OFF_RED + 32 * sizeof(double);
+  static constexpr size_t OFF_SPAN = OFF_RED + 32 * sizeof(double);      // lo[M], hi[M]
+  static constexpr size_t OFF_BAR = OFF_SPAN + (size_t)2 * M * sizeof(int);
   static constexpr size_t BYTES = OFF_BAR + sizeof(uint64_t);
   static_assert(N % CL == 0 && M % (2 * LP) == 0, "bad cluster split");
   static_assert(NT % MRMAX == 0, "bad column split");
@@ -82,18 +83,44 @@ __global__ void __launch_bounds__(YZ<N, CL>::NT, 2) k_yzpass(Fields fp0, int reg
   float2* twM = reinterpret_cast<float2*>(smem + Y::OFF_TWM);
   double* red = reinterpret_cast<double*>(smem + Y::OFF_RED);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Y::OFF_BAR);
+  int* s_lo = reinterpret_cast<int*>(smem + Y::OFF_SPAN);
+  int* s_hi = s_lo + M;
   const int t = threadIdx.x;
   const int r = CL > 1 ? (int)(blockIdx.x % CL) : 0;     // rank in the cluster (cluster along x)
   const int plane = (int)blockIdx.x / CL;
   DevState* ds = fp.ds;
   float2* Wp = fp.W + (long long)plane * N * ZP;
 
-  // ---- own rows ky in [r M, (r + 1) M): one bulk copy
+  // ---- supports [lo, hi) of a and c on the z lines of this CTA (local row i is
+  // y = CL i + r); outside them g = 0
+  bool mine = false;
+  for (int i = t; i < M; i += NT) {
+    int lo = 0, hi = N;
+    if (fp.span) {
+      const int2 sp = fp.span[(long long)plane * N + CL * i + r];
+      lo = N - sp.x;
+      hi = sp.y;
+    }
+    s_lo[i] = lo;
+    s_hi[i] = hi;
+    mine |= hi > lo;
+  }
   if (t == 0) {
     mbar_init(bar, 1);
     mbar_fence_init();
   }
-  __syncthreads();
+  const bool any_support = __syncthreads_or(mine);
+  if constexpr (CL == 1) {
+    // a plane without support has g = 0 on every line: a zero force, W not read
+    if (!any_support) {
+      for (int e = t; e < Y::E; e += NT)
+        if (e % ZP <= H) Wp[e] = make_float2(0.f, 0.f);
+      if (region >= 0 && t == 0) fp.part[region + blockIdx.x] = 0.0;
+      return;
+    }
+  }
+
+  // ---- own rows ky in [r M, (r + 1) M): one bulk copy
   if (t == 0) {
     mbar_expect_tx(bar, (uint32_t)Y::BLK);
     bulk_load(blk, Wp + (long long)r * M * ZP, (uint32_t)Y::BLK, bar);
@@ -160,6 +187,18 @@ __global__ void __launch_bounds__(YZ<N, CL>::NT, 2) k_yzpass(Fields fp0, int reg
   double eacc = 0.0;
   for (int q = 0; q < Y::ROUNDS; ++q) {
     const int i0 = q * 2 * LP;
+    bool round_support = false;
+#pragma unroll
+    for (int l = 0; l < 2 * LP; ++l) round_support |= s_hi[i0 + l] > s_lo[i0 + l];
+    if (!round_support) {
+      // every line of the round has g = 0: zero rows, no transforms
+      for (int i = t; i < 2 * LP * (H + 1); i += NT) {
+        const int l = i / (H + 1), k = i - l * (H + 1);
+        blk[(i0 + l) * ZP + k] = make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      continue;
+    }
     float2 v[Y::RMAX];
     {
       const int f = t / R2, a = t % R2;
@@ -191,10 +230,14 @@ __global__ void __launch_bounds__(YZ<N, CL>::NT, 2) k_yzpass(Fields fp0, int reg
         const long long lb = la + (long long)CL * N;
         const float* pa = fp.a;
         const float* pc = fp.c;
+        const int loa = s_lo[i0 + 2 * f], hia = s_hi[i0 + 2 * f];
+        const int lob = s_lo[i0 + 2 * f + 1], hib = s_hi[i0 + 2 * f + 1];
 #pragma unroll
         for (int d = 0; d < R2; ++d) {
           const int n = c + R1 * d;
-          const float aa = pa[la + n], ca = pc[la + n], ab = pa[lb + n], cb = pc[lb + n];
+          const bool ina = n >= loa && n < hia, inb = n >= lob && n < hib;
+          const float aa = ina ? pa[la + n] : 0.f, ca = ina ? pc[la + n] : 0.f;
+          const float ab = inb ? pa[lb + n] : 0.f, cb = inb ? pc[lb + n] : 0.f;
           const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
           const float ga = fmaf(aa, da, -ca), gb = fmaf(ab, db, -cb);
           e += da * (ga - ca) + db * (gb - cb);          // a d^2 - 2 c d

@@ -98,6 +98,52 @@ def test_gradient_and_energies(torch_cuda, N, n_sub):
         s.close()
 
 
+@pytest.mark.parametrize("N,n_sub,f_sky", [(32, 2, 0.6), (64, 3, 0.25), (128, 2, 0.4)])
+def test_gradient_three_passes_with_line_supports(torch_cuda, monkeypatch, N, n_sub, f_sky):
+    """The force z pass stages a and c only on each z line's support (R > 0 in some
+    subsample) and writes a zero force on tiles without support; grids up to 128^3
+    normally take the fused plane kernel, so the three passes are forced here.  A
+    support that missed an observed voxel would drop its a and c from the force."""
+    from paper_1306_1821_gb300 import bps
+    monkeypatch.setenv("BPS_FUSED_YZ", "0")
+    torch = torch_cuda
+    pb = Problem(N, n_sub=n_sub, n_bins=4, f_sky=f_sky)
+    assert (pb.R.reshape(n_sub, -1).max(0) == 0).mean() > 0.3   # a survey with unobserved lines
+    s = pb.gpu()
+    try:
+        g = torch.zeros((N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+        e = bps.bps_gradient(s.ctx, g)
+        a, c = model.local_fields(pb.counts, pb.R, pb.b, pb.nbar)
+        gh, lik = model.gradient_hat(pb.geom, pb.dh, pb.P, a, c)
+        assert rel_l2(g.cpu().numpy(), gh) < 1e-5
+        assert abs(e[1] - lik) < 1e-5 * (abs(lik) + np.sum(np.abs(a * grid.inverse(pb.dh, N) ** 2)))
+    finally:
+        s.close()
+
+
+def test_line_supports_follow_new_data(torch_cuda, monkeypatch):
+    """Uploading a second survey with a wider mask into the same context resets the
+    per-line supports: the force then matches the oracle on the new survey."""
+    from paper_1306_1821_gb300 import bps
+    monkeypatch.setenv("BPS_FUSED_YZ", "0")
+    torch = torch_cuda
+    N = 64
+    narrow = Problem(N, n_sub=2, n_bins=4, f_sky=0.15, seed=5)
+    wide = Problem(N, n_sub=2, n_bins=4, f_sky=0.9, seed=6)
+    s = narrow.gpu()
+    try:
+        bps.bps_set_data(s.ctx, torch.from_numpy(wide.counts).cuda(), torch.from_numpy(wide.R).cuda())
+        bps.bps_set_state(s.ctx, None, wide.P, wide.b, wide.nbar, 0)
+        bps.bps_set_spectrum(s.ctx, torch.from_numpy(wide.dh32).cuda())
+        g = torch.zeros((N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+        bps.bps_gradient(s.ctx, g)
+        a, c = model.local_fields(wide.counts, wide.R, wide.b, wide.nbar)
+        gh, _ = model.gradient_hat(wide.geom, wide.dh, wide.P, a, c)
+        assert rel_l2(g.cpu().numpy(), gh) < 1e-5
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("N,n_sub,moves", [(16, 1, 4), (32, 2, 3)])
 def test_hmc_moves_match_oracle(torch_cuda, N, n_sub, moves):
     from paper_1306_1821_gb300 import bps
