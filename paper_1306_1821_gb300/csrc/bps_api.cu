@@ -159,6 +159,7 @@ Fields fields(bps_ctx* c) {
   f.part = c->part;
   f.part_stride = c->part_stride;
   f.tw = c->tw;
+  f.grid_n = c->N;
   f.inv_nv = (float)(1.0 / (double)c->nv);
   f.mass_mode = (c->cfg.mass_mode != 0 || c->mnet) ? 1 : 0;
   f.n_bins = c->cfg.n_bins;
@@ -896,6 +897,11 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float*
   if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(nobs), no.data(), ns * sizeof(double));
   if (st != BPS_OK) return st;
   ctx->have_data[ch] = 1;
+  if (span_ch) {
+    // the rebuild writes a and c inside the supports only: zero them once here
+    CK(cudaMemsetAsync(f.a, 0, (size_t)ctx->nv * sizeof(float), s));
+    CK(cudaMemsetAsync(f.c, 0, (size_t)ctx->nv * sizeof(float), s));
+  }
   st = rebuild_chain(ctx, ch);
   if (st != BPS_OK) return st;
   CK(cudaStreamSynchronize(s));

@@ -545,12 +545,15 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   // L2), and the forward y pass starts on the planes the z pass wrote last.
   const long long L0 = (long long)(gridDim.x - 1 - blockIdx.x) * LINES;
   constexpr bool STAGED = MODE != Z_NOISE;
-  // Z_GRAD: support [lo, hi) of a and c on each line of the tile (whole lines
-  // without support information).  Outside it a = c = 0, so g = 0 there: only
-  // the support is staged, and a tile without support has g = 0 on every line,
-  // hence a zero force, written without reading W.
-  __shared__ int s_lo[MODE == Z_GRAD ? LINES : 1], s_hi[MODE == Z_GRAD ? LINES : 1];
-  if constexpr (MODE == Z_GRAD) {
+  // Z_GRAD, Z_SUMS: support [lo, hi) of R on each line of the tile (whole lines
+  // without support information).  Outside it R = 0, the counts are 0 and
+  // a = c = 0, so g = 0 and every term of the sums vanishes there: Z_GRAD stages
+  // a and c on the support only and gives a tile without support a zero force,
+  // written without reading W; Z_SUMS reads the data on the support only and
+  // gives such a tile zero sums.
+  constexpr bool SUPPORT = MODE == Z_GRAD || MODE == Z_SUMS;
+  __shared__ int s_lo[SUPPORT ? LINES : 1], s_hi[SUPPORT ? LINES : 1];
+  if constexpr (SUPPORT) {
     if (t < LINES) {
       if (fp.span) {
         const int2 sp = fp.span[L0 + t];
@@ -568,16 +571,21 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       mbar_fence_init();
     }
     __syncthreads();
-    if constexpr (MODE == Z_GRAD) {
+    if constexpr (SUPPORT) {
       bool any = false;
 #pragma unroll
       for (int l = 0; l < LINES; ++l) any |= s_hi[l] > s_lo[l];
       if (!any) {
-        for (int i = t; i < LINES * (H + 1); i += NTZ) {
-          const int l = i / (H + 1), k = i - l * (H + 1);
-          fp.W[(L0 + l) * ZP + k] = make_float2(0.f, 0.f);
+        if constexpr (MODE == Z_GRAD) {
+          for (int i = t; i < LINES * (H + 1); i += NTZ) {
+            const int l = i / (H + 1), k = i - l * (H + 1);
+            fp.W[(L0 + l) * ZP + k] = make_float2(0.f, 0.f);
+          }
+          if (za.region >= 0 && t == 0) fp.part[za.region + blockIdx.x] = 0.0;
+        } else {
+          const int nsub = ds->nsub;
+          for (int q = t; q < 3 * nsub; q += NTZ) fp.part[za.region + q * fp.part_stride + blockIdx.x] = 0.0;
         }
-        if (za.region >= 0 && t == 0) fp.part[za.region + blockIdx.x] = 0.0;
         return;
       }
     }
@@ -695,6 +703,8 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
     if constexpr (MODE == Z_SUMS) {
       const long long nv = (long long)N * N * N;
       const int nsub = ds->nsub;
+      const int loa = f < LP ? s_lo[2 * f] : 0, hia = f < LP ? s_hi[2 * f] : 0;
+      const int lob = f < LP ? s_lo[2 * f + 1] : 0, hib = f < LP ? s_hi[2 * f + 1] : 0;
       for (int l = 0; l < nsub; ++l) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (f < LP) {
@@ -703,9 +713,11 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
 #pragma unroll
           for (int d = 0; d < R2; ++d) {
             const int n = c + R1 * d;
+            const bool ina = n >= loa && n < hia, inb = n >= lob && n < hib;
             const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
-            const float ra = rr[la + n], rb = rr[lb + n];
-            s1 += (float)cn[la + n] * da + (float)cn[lb + n] * db;
+            const float ra = ina ? rr[la + n] : 0.f, rb = inb ? rr[lb + n] : 0.f;
+            const float na = ina ? (float)cn[la + n] : 0.f, nb = inb ? (float)cn[lb + n] : 0.f;
+            s1 += na * da + nb * db;
             s2 += ra * da + rb * db;
             s3 += ra * da * da + rb * db * db;
           }
@@ -779,6 +791,8 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 
 // a_i = sum_l b_l^2 Nbar_l R^l_i,  c_i = sum_l b_l (N^l_i - Nbar_l R^l_i)  (Eq. Wiener_Posterior_force);
 // the counts are zero wherever R = 0 (checked by set_data), so no mask is needed.
+// With per-line supports only the voxels inside them are computed: outside,
+// a = c = 0, which the data upload wrote once.
 __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int region) {
   const Fields fp = at_chain(fp0, blockIdx.y);
   __shared__ float s_a[MAXS], s_b[MAXS], s_bn[MAXS];
@@ -794,7 +808,14 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
   __syncthreads();
   float acc = 0.f, comp = 0.f;   // FP32 with Kahan compensation per thread; FP64 across the block
   const long long n4 = nv / 4;
+  const int n_grid = fp.grid_n;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
+    if (fp.span) {
+      const long long line = (4 * i) / n_grid;
+      const int z = (int)(4 * i - line * n_grid);
+      const int2 sp = fp.span[line];
+      if (z < n_grid - sp.x || z >= sp.y) continue;
+    }
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Cc = A;
     for (int l = 0; l < nsub; ++l) {
       const float4 r = reinterpret_cast<const float4*>(fp.R + l * nv)[i];

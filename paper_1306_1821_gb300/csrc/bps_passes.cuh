@@ -38,6 +38,7 @@ struct Fields {
   double* part;           // per-block partial sums (FP64)
   int part_stride;        // doubles between consecutive quantities of one region
   const float2* tw;       // W_N^j = exp(-2 pi i j / N), j < N (FP64-rounded)
+  int grid_n;             // N
   float inv_nv;           // 1 / N^3
   int mass_mode;
   int n_bins, n_mass;     // entries of the P-bin and mass-bin threshold tables
