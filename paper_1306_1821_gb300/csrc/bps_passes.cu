@@ -512,11 +512,8 @@ struct ZSmem {
   using C = Cfg<N>;
   static constexpr int LINES = 2 * LP;
   static constexpr size_t BUF = (size_t)LP * (N + C::RMAX) * sizeof(float2);
-  static constexpr size_t AC = MODE == Z_GRAD ? (size_t)LINES * N * sizeof(float) : 0;
   static constexpr size_t OFF_BUF = 0;
-  static constexpr size_t OFF_A = BUF;
-  static constexpr size_t OFF_C = OFF_A + AC;
-  static constexpr size_t OFF_TW = OFF_C + AC;
+  static constexpr size_t OFF_TW = BUF;
   static constexpr size_t OFF_RED = OFF_TW + (size_t)N * sizeof(float2);
   static constexpr size_t OFF_BAR = OFF_RED + 32 * sizeof(double);
   static constexpr size_t BYTES = OFF_BAR + sizeof(uint64_t);
@@ -533,8 +530,6 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   constexpr int LINES = L::LINES;
   extern __shared__ __align__(128) unsigned char smem[];
   float2* s_buf = reinterpret_cast<float2*>(smem + L::OFF_BUF);
-  float* s_a = reinterpret_cast<float*>(smem + L::OFF_A);
-  float* s_c = reinterpret_cast<float*>(smem + L::OFF_C);
   float2* s_tw = reinterpret_cast<float2*>(smem + L::OFF_TW);
   double* s_red = reinterpret_cast<double*>(smem + L::OFF_RED);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
@@ -547,10 +542,9 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   constexpr bool STAGED = MODE != Z_NOISE;
   // Z_GRAD, Z_SUMS: support [lo, hi) of R on each line of the tile (whole lines
   // without support information).  Outside it R = 0, the counts are 0 and
-  // a = c = 0, so g = 0 and every term of the sums vanishes there: Z_GRAD stages
-  // a and c on the support only and gives a tile without support a zero force,
-  // written without reading W; Z_SUMS reads the data on the support only and
-  // gives such a tile zero sums.
+  // a = c = 0, so g = 0 and every term of the sums vanishes there: both read a
+  // and c (or the data) on the support only, and give a tile without support a
+  // zero force, written without reading W, or zero sums.
   constexpr bool SUPPORT = MODE == Z_GRAD || MODE == Z_SUMS;
   __shared__ int s_lo[SUPPORT ? LINES : 1], s_hi[SUPPORT ? LINES : 1];
   if constexpr (SUPPORT) {
@@ -597,25 +591,8 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       } else {
         const float2* src = (MODE == Z_C2R) ? za.src : fp.W;
         constexpr uint32_t SB = LINES * ZP * sizeof(float2);
-        if constexpr (MODE == Z_GRAD) {
-          // supports are multiples of 4 floats: 16-byte aligned bulk copies
-          uint32_t acb = 0;
-          for (int l = 0; l < LINES; ++l)
-            if (s_hi[l] > s_lo[l]) acb += (uint32_t)(s_hi[l] - s_lo[l]) * sizeof(float);
-          mbar_expect_tx(bar, SB + 2 * acb);
-          bulk_load(s_buf, src + L0 * ZP, SB, bar);
-          for (int l = 0; l < LINES; ++l) {
-            if (s_hi[l] > s_lo[l]) {
-              const uint32_t nb = (uint32_t)(s_hi[l] - s_lo[l]) * sizeof(float);
-              const long long g0 = (L0 + l) * N + s_lo[l];
-              bulk_load(s_a + l * N + s_lo[l], fp.a + g0, nb, bar);
-              bulk_load(s_c + l * N + s_lo[l], fp.c + g0, nb, bar);
-            }
-          }
-        } else {
-          mbar_expect_tx(bar, SB);
-          bulk_load(s_buf, src + L0 * ZP, SB, bar);
-        }
+        mbar_expect_tx(bar, SB);
+        bulk_load(s_buf, src + L0 * ZP, SB, bar);
       }
     }
   }
@@ -705,6 +682,11 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       const int nsub = ds->nsub;
       const int loa = f < LP ? s_lo[2 * f] : 0, hia = f < LP ? s_hi[2 * f] : 0;
       const int lob = f < LP ? s_lo[2 * f + 1] : 0, hib = f < LP ? s_hi[2 * f + 1] : 0;
+      // per-warp FP64 sums of all 3 nsub quantities, then one pass over the warps
+      // (the same additions, in the same order, as one block sum per quantity)
+      constexpr int NW = (NTZ + 31) / 32;
+      __shared__ double s_ws[NW][3 * MAXS];
+      const int lane = t & 31, w = t >> 5;
       for (int l = 0; l < nsub; ++l) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (f < LP) {
@@ -722,29 +704,36 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
             s3 += ra * da * da + rb * db * db;
           }
         }
-        double t1 = block_sum<NTZ>((double)s1, s_red);
-        double t2 = block_sum<NTZ>((double)s2, s_red);
-        double t3 = block_sum<NTZ>((double)s3, s_red);
-        if (t == 0) {
-          fp.part[za.region + (3 * l + 0) * fp.part_stride + blockIdx.x] = t1;
-          fp.part[za.region + (3 * l + 1) * fp.part_stride + blockIdx.x] = t2;
-          fp.part[za.region + (3 * l + 2) * fp.part_stride + blockIdx.x] = t3;
+        const double t1 = warp_sum((double)s1), t2 = warp_sum((double)s2), t3 = warp_sum((double)s3);
+        if (lane == 0) {
+          s_ws[w][3 * l + 0] = t1;
+          s_ws[w][3 * l + 1] = t2;
+          s_ws[w][3 * l + 2] = t3;
         }
+      }
+      __syncthreads();
+      for (int q = t; q < 3 * nsub; q += NTZ) {
+        double r = 0.0;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r += s_ws[i][q];
+        fp.part[za.region + q * fp.part_stride + blockIdx.x] = r;
       }
       return;
     }
     // Z_GRAD: the local force g = a delta - c (Eq. Wiener_Posterior_force) and the
-    // likelihood energy (1/2) sum (a delta^2 - 2 c delta)
+    // likelihood energy (1/2) sum (a delta^2 - 2 c delta).  a and c are read from
+    // global memory on the support only (not staged: shared memory would cap the
+    // resident tiles of this latency-bound pass).
     float e = 0.f;
     if (f < LP) {
-      const int ra = (2 * f) * N, rb = ra + N;
       const int loa = s_lo[2 * f], hia = s_hi[2 * f], lob = s_lo[2 * f + 1], hib = s_hi[2 * f + 1];
 #pragma unroll
       for (int d = 0; d < R2; ++d) {
         const int n = c + R1 * d;
         const bool ina = n >= loa && n < hia, inb = n >= lob && n < hib;
-        const float aa = ina ? s_a[ra + n] : 0.f, ca = ina ? s_c[ra + n] : 0.f;
-        const float ab = inb ? s_a[rb + n] : 0.f, cb = inb ? s_c[rb + n] : 0.f;
+        const long long ga0 = (L0 + 2 * f) * N + n, gb0 = ga0 + N;
+        const float aa = ina ? __ldg(fp.a + ga0) : 0.f, ca = ina ? __ldg(fp.c + ga0) : 0.f;
+        const float ab = inb ? __ldg(fp.a + gb0) : 0.f, cb = inb ? __ldg(fp.c + gb0) : 0.f;
         const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
         const float ga = fmaf(aa, da, -ca), gb = fmaf(ab, db, -cb);
         e += da * (ga - ca) + db * (gb - cb);   // a d^2 - 2 c d
