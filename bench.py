@@ -310,16 +310,21 @@ def run_ours(args):
         dist.barrier()
     acc_rate = float(np.mean(rec[:, -1])) if len(rec) else float("nan")
 
-    # ---- end to end through the public API with host buffers: upload the
-    # survey from pinned memory, one Gibbs iteration, read the chain record back
+    # ---- end to end through the public API with host buffers: every step
+    # uploads its survey from pinned memory, runs one Gibbs iteration and reads
+    # the chain record back.  The upload of step k + 1 is staged
+    # (bps_stage_data_host_u16) before step k runs, so it overlaps step k; all
+    # uploads and read-backs lie inside the timed region.
     k_e2e = min(args.steps, 20)
     cnt_h = torch.from_numpy(counts.astype(np.uint16)).pin_memory().numpy()   # counts <= 65535: 16-bit upload
     R_h = torch.from_numpy(R).pin_memory().numpy()
     rec_h = torch.zeros(s.rec_len, dtype=torch.float64).pin_memory().numpy()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        bps.bps_set_data_host_u16(s.ctx, cnt_h, R_h)
+    bps.bps_stage_data_host_u16(s.ctx, cnt_h, R_h)
+    for k in range(k_e2e):
+        if k + 1 < k_e2e:
+            bps.bps_stage_data_host_u16(s.ctx, cnt_h, R_h)
         out = bps.bps_gibbs_iterate(s.ctx, 1, s.rec_len)
         rec_h[:] = out[0]
     torch.cuda.synchronize(dev)
@@ -413,7 +418,10 @@ def run_ours(args):
                                   "frac": leap_bytes / (leap_ms * 1e-3) / 1e9 / peak},
             "e2e": {"value": e2e_units / e2e_secs, "unit": UNIT,
                     "h2d_bytes_per_step": int(cnt_h.nbytes + R_h.nbytes),
-                    "d2h_bytes_per_step": int(8 * s.rec_len)},
+                    "d2h_bytes_per_step": int(8 * s.rec_len),
+                    "steps": k_e2e,
+                    "pipelined": "each step's survey upload (bps_stage_data_host_u16) runs during the previous "
+                                 "step's Gibbs iteration"},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }

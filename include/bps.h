@@ -110,6 +110,22 @@ bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R
  * width; counts are bounded by 65535 in any case): a quarter less to copy. */
 bps_status bps_set_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R);
 
+/* Starts the upload of a survey (counts uint16 and R float32 [n_sub][N][N][N],
+ * host arrays, as for bps_set_data_host_u16) into the context's second data
+ * slot and returns without waiting: copies and data check run on the
+ * context's own streams, beside whatever the caller queues next.  The next
+ * call that uses the data (bps_gibbs_iterate, bps_hmc_step, bps_sample_*,
+ * bps_jump, bps_gradient, ...) first activates the oldest staged survey: it
+ * waits for the upload, takes the data constants of Sec. 3.6 from the check
+ * and rebuilds a and c (Eq. Wiener_Posterior_force).  A survey that fails the
+ * checks of bps_set_data is not activated; the call that met it returns
+ * BPS_EINVAL, having run on the previous survey.  At most two surveys can be
+ * staged ahead (BPS_ESTATE otherwise); the host arrays must stay unchanged
+ * until the call that activates them returns.  With pinned host memory the
+ * copies overlap the Gibbs iterations queued after them, so the upload of
+ * survey k + 1 can run during iteration k. */
+bps_status bps_stage_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R);
+
 /* Chain state (Sec. 3.2): delta_dev float32 [N][N][N] real field (its mean is
  * dropped: the k = 0 mode is held at zero), P [n_bins], b [n_sub], nbar [n_sub]
  * host FP64, and the iteration counter of the random streams.  P also becomes

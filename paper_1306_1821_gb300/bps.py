@@ -44,6 +44,7 @@ _SIGS = {
     "bps_set_data": ([_P, _P, _P], ctypes.c_int),
     "bps_set_data_host": ([_P, _P, _P], ctypes.c_int),
     "bps_set_data_host_u16": ([_P, _P, _P], ctypes.c_int),
+    "bps_stage_data_host_u16": ([_P, _P, _P], ctypes.c_int),
     "bps_z_line_pairs": ([_P], ctypes.c_int),
     "bps_adapt_step_size": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D], ctypes.c_int),
     "bps_set_preconditioner": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
@@ -179,6 +180,17 @@ def bps_set_data_host_u16(ctx, counts, R):
     c = np.ascontiguousarray(counts, dtype=np.uint16)
     r = np.ascontiguousarray(R, dtype=np.float32)
     _check(ctx, load().bps_set_data_host_u16(ctx, c.ctypes.data_as(_P), r.ctypes.data_as(_P)))
+
+
+def bps_stage_data_host_u16(ctx, counts, R):
+    """Asynchronous upload (see the C declaration).  The arrays are passed without
+    conversion, so that the library copies the caller's memory after this call
+    returns: uint16 and float32, C-contiguous, and unchanged until the next call
+    that uses the data returns (pinned memory for the copies to overlap)."""
+    for a, dt in ((counts, np.uint16), (R, np.float32)):
+        if not (isinstance(a, np.ndarray) and a.dtype == dt and a.flags.c_contiguous):
+            raise TypeError(f"bps_stage_data_host_u16 needs C-contiguous {np.dtype(dt).name} arrays")
+    _check(ctx, load().bps_stage_data_host_u16(ctx, counts.ctypes.data_as(_P), R.ctypes.data_as(_P)))
 
 
 def bps_set_state(ctx, delta, P, b, nbar, iteration=0):

@@ -81,6 +81,16 @@ struct bps_ctx {
   cudaStream_t copy_stream[2] = {nullptr, nullptr};   // counts, response: two copies in flight
   cudaEvent_t stage_copied[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaEvent_t stage_free[2] = {nullptr, nullptr};
+  // staged surveys (bps_stage_data_host_u16): each chain has two data slots;
+  // an upload fills the slot after the last one used, on up_stream, and waits
+  // (FIFO, at most two) until an operation that uses the data activates it
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_after_main = nullptr;     // orders an upload after earlier work on the main stream
+  std::vector<cudaEvent_t> slot_ready;     // [chain][slot]: the upload into that slot is complete
+  std::vector<std::vector<int>> pending;   // per chain: staged slots, oldest first
+  std::vector<int> next_slot;              // per chain: the slot the next upload fills
+  double* dpart = nullptr;                 // data-kernel partials [slot][chain][MAXS][4][blocks]
+  long long dpart_cstride = 0;
   bool graph_jump = false;
   uint64_t graph_launches = 0;   // kernels in one replay of the graph
   // leapfrog kernel timing (bps_profile)
@@ -154,6 +164,8 @@ Fields fields(bps_ctx* c) {
   f.R = c->R;
   f.span = c->span;
   f.span_stride = (long long)c->N * c->N;
+  f.data_slot = (long long)c->max_sub * c->nv * c->batch;
+  f.span_slot = (long long)c->N * c->N * c->batch;
   f.n_sub = c->max_sub;
   f.ds = c->ds;
   f.part = c->part;
@@ -273,6 +285,10 @@ bps_status check_status(bps_ctx* ctx) {
       any |= st;
     }
   }
+  if (any & ST_BADDATA)
+    return fail(ctx, BPS_EINVAL,
+                "invalid survey data (R < 0 or non-finite, a count outside 0..65535, a count > 0 where R = 0, "
+                "or a subsample without observed voxels); the previous survey stays active");
   if (any & ST_TIMEOUT) return fail(ctx, BPS_ETIMEOUT, "a tile copy did not complete within the wait limit");
   if (any & ST_NONFINITE) return fail(ctx, BPS_ENUMERIC, "non-finite energy difference; move rejected");
   if (any) return fail(ctx, BPS_ENUMERIC, "a scalar draw failed (no acceptance within the attempt bound or a non-positive sum)");
@@ -481,11 +497,17 @@ bps_status gibbs_once(bps_ctx* ctx, double* rec, int rec_len, long long iter_str
   return BPS_OK;
 }
 
+bps_status commit_data(bps_ctx* ctx, int ch);
+
+// Activates the oldest staged survey of each chain, then requires data.
 bps_status need_data(bps_ctx* ctx) {
   if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
   if (ctx->is_batch) return fail(ctx, BPS_EINVAL, "a batch context takes the bps_batch_* calls");
-  for (int ch = 0; ch < ctx->batch; ++ch)
+  for (int ch = 0; ch < ctx->batch; ++ch) {
+    bps_status st = commit_data(ctx, ch);
+    if (st != BPS_OK) return st;
     if (!ctx->have_data[ch]) return fail(ctx, BPS_ESTATE, "bps_set_data has not been called");
+  }
   return BPS_OK;
 }
 
@@ -517,6 +539,10 @@ void drop_graph(bps_ctx* c) {
 }
 
 void free_streams(bps_ctx* c) {
+  // staged uploads may still be writing the data slots
+  if (c->up_stream) cudaStreamSynchronize(c->up_stream);
+  for (int i = 0; i < 2; ++i)
+    if (c->copy_stream[i]) cudaStreamSynchronize(c->copy_stream[i]);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
   for (int i = 0; i < 2; ++i) {
@@ -531,6 +557,15 @@ void free_streams(bps_ctx* c) {
   }
   cudaFree(c->stage);
   c->stage = nullptr;
+  if (c->up_stream) cudaStreamDestroy(c->up_stream);
+  c->up_stream = nullptr;
+  if (c->up_after_main) cudaEventDestroy(c->up_after_main);
+  c->up_after_main = nullptr;
+  for (cudaEvent_t& e : c->slot_ready)
+    if (e) cudaEventDestroy(e);
+  c->slot_ready.clear();
+  cudaFree(c->dpart);
+  c->dpart = nullptr;
 }
 
 void free_all(bps_ctx* c) {
@@ -729,6 +764,8 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
   ctx->n_mass = cfg->n_bins;
   ctx->chain_cap = ids.empty() ? 1024 : 0;
   ctx->have_data.assign(B, 0);
+  ctx->pending.assign(B, std::vector<int>());
+  ctx->next_slot.assign(B, 1);   // slot 0 (all zero) stays active until a first survey is valid
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -746,7 +783,7 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
 
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
   const size_t sb = ctx->n_spec * sizeof(float2) * B, rb = (size_t)ctx->nv * sizeof(float) * B;
-  const size_t span_bytes = (size_t)grid_n * grid_n * sizeof(int2) * B;
+  const size_t span_bytes = 2 * (size_t)grid_n * grid_n * sizeof(int2) * B;   // two data slots
   const int rec_len = cfg->n_bins + 2 * max_sub + 2;
   bool ok = alloc((void**)&ctx->dh[0], sb) && alloc((void**)&ctx->dh[1], sb) && alloc((void**)&ctx->ph, sb) &&
             alloc((void**)&ctx->W, sb) && alloc((void**)&ctx->a, rb) && alloc((void**)&ctx->c, rb) &&
@@ -800,12 +837,20 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
 }
 
 // ------------------------------------------------------------------ per-chain operations
-bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float* R, bool host, bool c16 = false) {
+// Starts the upload of one chain's survey into its next data slot: (host
+// arrays) copies through the two staging slots on the copy streams, then the
+// check-and-compress kernel of each subsample on up_stream, which also widens
+// the slot's per-line supports and leaves its partial sums in dpart.  Nothing
+// waits on the host; commit_data activates the slot.
+bps_status stage_data(bps_ctx* ctx, int ch, const void* counts, const float* R, bool host, bool c16) {
   if (!counts || !R) return fail(ctx, BPS_EINVAL, "null argument");
-  cudaStream_t s = ctx->stream;
+  if (ctx->pending[ch].size() >= 2)
+    return fail(ctx, BPS_ESTATE, "two surveys are already staged; run an operation that uses the data first");
   const int ns = ctx->nsub[ch];
+  const int B = ctx->batch;
+  const int blocks = ctx->rebuild_blocks;
   if (!ctx->cnt) {
-    const size_t total = (size_t)ctx->max_sub * ctx->nv * ctx->batch;
+    const size_t total = 2 * (size_t)ctx->max_sub * ctx->nv * B;   // two data slots
     if (cudaMalloc((void**)&ctx->cnt, total * sizeof(uint16_t)) != cudaSuccess ||
         cudaMalloc((void**)&ctx->R, total * sizeof(float)) != cudaSuccess) {
       cudaGetLastError();
@@ -815,12 +860,23 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float*
       ctx->R = nullptr;
       return fail(ctx, BPS_ENOMEM, "device allocation of the survey data failed");
     }
-    CK(cudaMemsetAsync(ctx->cnt, 0, total * sizeof(uint16_t), s));
-    CK(cudaMemsetAsync(ctx->R, 0, total * sizeof(float), s));
+    CK(cudaMemsetAsync(ctx->cnt, 0, total * sizeof(uint16_t), ctx->stream));
+    CK(cudaMemsetAsync(ctx->R, 0, total * sizeof(float), ctx->stream));
   }
-  Fields f = fields_at(ctx, ch);
-  uint16_t* cnt_ch = const_cast<uint16_t*>(f.cnt);
-  float* R_ch = const_cast<float*>(f.R);
+  if (!ctx->up_stream) {
+    ctx->dpart_cstride = (long long)MAXS * 4 * blocks;
+    bool ok = cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->up_after_main, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc((void**)&ctx->dpart, (size_t)2 * B * ctx->dpart_cstride * sizeof(double)) == cudaSuccess;
+    ctx->slot_ready.assign(2 * (size_t)B, nullptr);
+    for (size_t i = 0; i < ctx->slot_ready.size() && ok; ++i)
+      ok = cudaEventCreateWithFlags(&ctx->slot_ready[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      free_streams(ctx);
+      return fail(ctx, BPS_ENOMEM, "upload streams and buffers could not be allocated");
+    }
+  }
   const size_t slot_bytes = (size_t)ctx->nv * (sizeof(int32_t) + sizeof(float));
   if (host && !ctx->stage) {
     bool ok = cudaMalloc((void**)&ctx->stage, 2 * slot_bytes) == cudaSuccess;
@@ -835,21 +891,44 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float*
       return fail(ctx, BPS_ENOMEM, "staging buffers for the host upload could not be allocated");
     }
   }
-  const int blocks = ctx->rebuild_blocks;
-  // the data kernels widen this chain's per-line supports from empty
-  int2* span_ch = ctx->span ? ctx->span + (size_t)ch * ctx->N * ctx->N : nullptr;
-  if (span_ch) CK(cudaMemsetAsync(span_ch, 0, (size_t)ctx->N * ctx->N * sizeof(int2), s));
-  // per-subsample partial sums side by side (4 quantities x blocks each), read back once
-  double* part = ctx->part + ch * ctx->part_cstride;
-  if ((long long)ns * 4 * blocks > ctx->part_cstride) return fail(ctx, BPS_EINVAL, "too many subsamples");
-  if (host) CK(cudaEventRecord(ctx->stage_free[0], s));   // orders the copies after earlier work on s
-  if (host) CK(cudaEventRecord(ctx->stage_free[1], s));
+  const int slot = ctx->next_slot[ch];
+  Fields f = fields_at(ctx, ch);
+  uint16_t* cnt_ch = const_cast<uint16_t*>(f.cnt) + slot * f.data_slot;
+  float* R_ch = const_cast<float*>(f.R) + slot * f.data_slot;
+  int2* span_ch = f.span ? const_cast<int2*>(f.span) + slot * f.span_slot : nullptr;
+  double* part = ctx->dpart + ((size_t)slot * B + ch) * ctx->dpart_cstride;
+  cudaStream_t up = ctx->up_stream;
+  // the slot may hold the survey that work already queued on the main stream reads
+  CK(cudaEventRecord(ctx->up_after_main, ctx->stream));
+  CK(cudaStreamWaitEvent(up, ctx->up_after_main, 0));
+  // the data kernels widen the slot's per-line supports from empty
+  if (span_ch) CK(cudaMemsetAsync(span_ch, 0, (size_t)ctx->N * ctx->N * sizeof(int2), up));
+  if (host) CK(cudaEventRecord(ctx->stage_free[0], up));   // orders the copies after earlier uploads
+  if (host) CK(cudaEventRecord(ctx->stage_free[1], up));
   const size_t csz = c16 ? sizeof(uint16_t) : sizeof(int32_t);
   for (int l = 0; l < ns; ++l) {
     const void* cl = static_cast<const char*>(counts) + (size_t)l * ctx->nv * csz;
     const float* rl = R + (size_t)l * ctx->nv;
+    if (host && c16) {
+      // 16-bit counts are the storage format: copy straight into the slot, then
+      // check in place (no staging round trip through device memory)
+      uint16_t* cdst = cnt_ch + (size_t)l * ctx->nv;
+      float* rdst = R_ch + (size_t)l * ctx->nv;
+      const int sl = l & 1;
+      for (int k = 0; k < 2; ++k) CK(cudaStreamWaitEvent(ctx->copy_stream[k], ctx->stage_free[sl], 0));
+      CK(cudaMemcpyAsync(cdst, cl, ctx->nv * csz, cudaMemcpyHostToDevice, ctx->copy_stream[0]));
+      CK(cudaMemcpyAsync(rdst, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_stream[1]));
+      for (int k = 0; k < 2; ++k) {
+        CK(cudaEventRecord(ctx->stage_copied[sl][k], ctx->copy_stream[k]));
+        CK(cudaStreamWaitEvent(up, ctx->stage_copied[sl][k], 0));
+      }
+      launch_data16(cdst, rdst, nullptr, nullptr, ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, span_ch,
+                    ctx->N, up);
+      LAUNCHED(ctx, 1);
+      continue;
+    }
     if (host) {
-      // copy subsample l into slot l % 2 once the data kernel of subsample l - 2 has read it
+      // copy subsample l into staging slot l % 2 once the data kernel of subsample l - 2 has read it
       const int sl = l & 1;
       void* ctmp = ctx->stage + sl * slot_bytes;
       float* rtmp = reinterpret_cast<float*>(ctx->stage + sl * slot_bytes + (size_t)ctx->nv * sizeof(int32_t));
@@ -858,54 +937,58 @@ bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float*
       CK(cudaMemcpyAsync(rtmp, rl, ctx->nv * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_stream[1]));
       for (int k = 0; k < 2; ++k) {
         CK(cudaEventRecord(ctx->stage_copied[sl][k], ctx->copy_stream[k]));
-        CK(cudaStreamWaitEvent(s, ctx->stage_copied[sl][k], 0));
+        CK(cudaStreamWaitEvent(up, ctx->stage_copied[sl][k], 0));
       }
       cl = ctmp;
       rl = rtmp;
     }
     if (c16)
       launch_data16(static_cast<const uint16_t*>(cl), rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv,
-                    ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, span_ch, ctx->N, s);
+                    ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, span_ch, ctx->N, up);
     else
       launch_data(static_cast<const int32_t*>(cl), rl, cnt_ch + (size_t)l * ctx->nv, R_ch + (size_t)l * ctx->nv,
-                  ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, span_ch, ctx->N, s);
+                  ctx->nv, part + (size_t)l * 4 * blocks, blocks, blocks, span_ch, ctx->N, up);
     LAUNCHED(ctx, 1);
-    if (host) CK(cudaEventRecord(ctx->stage_free[l & 1], s));
+    if (host) CK(cudaEventRecord(ctx->stage_free[l & 1], up));
   }
-  std::vector<double> hp((size_t)ns * 4 * blocks);
-  CK(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  std::vector<double> sR(ns), sB(ns), no(ns);
-  double bad = 0.0;
-  for (int l = 0; l < ns; ++l) {
-    double v[4] = {0, 0, 0, 0};
-    for (int q = 0; q < 4; ++q)
-      for (int b = 0; b < blocks; ++b) v[q] += hp[((size_t)l * 4 + q) * blocks + b];
-    sR[l] = v[0];
-    sB[l] = v[1];
-    no[l] = v[2];
-    bad += v[3];
-  }
-  if (bad > 0.0) {
-    ctx->have_data[ch] = 0;
-    return fail(ctx, BPS_EINVAL, "invalid survey data: R < 0 or non-finite, a count outside 0..65535, or a count > 0 where R = 0");
-  }
-  for (int l = 0; l < ns; ++l)
-    if (!(no[l] > 0.0)) return fail(ctx, BPS_EINVAL, "a subsample has no observed voxel (R > 0)");
-  bps_status st = ds_write_bytes(ctx, ch, DS_OFF(sumR), sR.data(), ns * sizeof(double));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(sumB), sB.data(), ns * sizeof(double));
-  if (st == BPS_OK) st = ds_write_bytes(ctx, ch, DS_OFF(nobs), no.data(), ns * sizeof(double));
-  if (st != BPS_OK) return st;
-  ctx->have_data[ch] = 1;
-  if (span_ch) {
-    // the rebuild writes a and c inside the supports only: zero them once here
+  CK(cudaEventRecord(ctx->slot_ready[2 * (size_t)ch + slot], up));
+  ctx->pending[ch].push_back(slot);
+  ctx->next_slot[ch] = 1 - slot;
+  return BPS_OK;
+}
+
+// Activates the oldest staged survey of chain `ch`, in order on the main
+// stream: waits for its upload, then the commit kernel (data constants, or
+// ST_BADDATA and the previous slot kept), then a and c rebuilt on the active
+// slot (zeroed first where the supports limit the rebuild).
+bps_status commit_data(bps_ctx* ctx, int ch) {
+  if (ctx->pending[ch].empty()) return BPS_OK;
+  const int slot = ctx->pending[ch].front();
+  ctx->pending[ch].erase(ctx->pending[ch].begin());
+  cudaStream_t s = ctx->stream;
+  CK(cudaStreamWaitEvent(s, ctx->slot_ready[2 * (size_t)ch + slot], 0));
+  launch_commit_data(ctx->ds + ch, ctx->dpart + ((size_t)slot * ctx->batch + ch) * ctx->dpart_cstride,
+                     ctx->dpart_cstride, ctx->rebuild_blocks, slot, 1, s);
+  LAUNCHED(ctx, 1);
+  Fields f = fields_at(ctx, ch);
+  if (f.span) {
     CK(cudaMemsetAsync(f.a, 0, (size_t)ctx->nv * sizeof(float), s));
     CK(cudaMemsetAsync(f.c, 0, (size_t)ctx->nv * sizeof(float), s));
   }
-  st = rebuild_chain(ctx, ch);
+  ctx->have_data[ch] = 1;
+  return rebuild_chain(ctx, ch);
+}
+
+// The synchronous upload: stage, activate every staged survey in order, and
+// report invalid data.
+bps_status set_data_chain(bps_ctx* ctx, int ch, const void* counts, const float* R, bool host, bool c16 = false) {
+  bps_status st = stage_data(ctx, ch, counts, R, host, c16);
+  while (st == BPS_OK && !ctx->pending[ch].empty()) st = commit_data(ctx, ch);
   if (st != BPS_OK) return st;
-  CK(cudaStreamSynchronize(s));
-  return BPS_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  st = check_status(ctx);
+  if (st != BPS_OK) ctx->have_data[ch] = 0;
+  return st;
 }
 
 bps_status set_state_chain(bps_ctx* ctx, int ch, const float* delta_dev, const double* P, const double* b,
@@ -1208,6 +1291,11 @@ bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R
 bps_status bps_set_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R) {
   if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
   return set_data_chain(ctx, 0, counts, R, true, true);
+}
+
+bps_status bps_stage_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R) {
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
+  return stage_data(ctx, 0, counts, R, true, true);
 }
 
 bps_status bps_set_state(bps_ctx* ctx, const float* delta_dev, const double* P, const double* b, const double* nbar,

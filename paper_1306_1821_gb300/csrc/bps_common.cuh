@@ -275,10 +275,12 @@ struct DevState {
   unsigned long long seed;           // Philox key
   int nsub;                          // galaxy subsamples of this chain
   int rec_idx;                       // next slot of the chain record buffer
+  int dslot;                         // active survey-data slot (Fields::data_slot)
+  int pad2;
   unsigned long long iteration;
   unsigned long long n_moves, n_accepted;
 };
 
-enum StatusBits : int { ST_OK = 0, ST_NONFINITE = 1, ST_DRAW_FAIL = 2 };
+enum StatusBits : int { ST_OK = 0, ST_NONFINITE = 1, ST_DRAW_FAIL = 2, ST_BADDATA = 8 };
 
 }  // namespace bps

@@ -281,6 +281,40 @@ __global__ void k_abar(ScalarArgs a0, int region, int nblk) {
   if (threadIdx.x == 0) a.ds->abar = s * a.inv_nv;
 }
 
+// ------------------------------------------------------------------ survey commit
+// Activates a survey uploaded into data slot `slot`: sums the data kernel's
+// per-block partials of each subsample (sum R, sum N^2/R, observed voxels,
+// invalid voxels; 4 x nblk doubles per subsample) in a fixed order, and either
+// writes the data constants of Secs. 3.5-3.6 and makes the slot active, or, for
+// invalid data or a subsample without observed voxels, flags ST_BADDATA and
+// keeps the previous slot.  One block per chain.
+__global__ void k_commit_data(DevState* ds0, const double* part0, long long cstride, int nblk, int slot) {
+  DevState* ds = ds0 + blockIdx.x;
+  const double* part = part0 + blockIdx.x * cstride;
+  __shared__ double sh[32];
+  __shared__ double s_v[MAXS][4];
+  const int nsub = ds->nsub;
+  for (int l = 0; l < nsub; ++l)
+    for (int q = 0; q < 4; ++q) {
+      const double v = sum_partials(part + ((size_t)l * 4 + q) * nblk, nblk, sh);
+      if (threadIdx.x == 0) s_v[l][q] = v;
+    }
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    for (int l = 0; l < nsub; ++l) ok = ok && s_v[l][3] == 0.0 && s_v[l][2] > 0.0;
+    if (!ok) {
+      atomicOr(&ds->status, ST_BADDATA);
+    } else {
+      for (int l = 0; l < nsub; ++l) {
+        ds->sumR[l] = s_v[l][0];
+        ds->sumB[l] = s_v[l][1];
+        ds->nobs[l] = s_v[l][2];
+      }
+      ds->dslot = slot;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ jump move
 // HMC in theta = ln P with the whitened field fixed (Sec. 4.3, App. C).
 // Mass mu_m = max(1, abar P_ref_m sigma_m / (4 V_cell P_m)): built from the
@@ -455,6 +489,10 @@ void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long 
   k_record<<<dim3(1, nch), MAXB, 0, s>>>(a, rec_dev, rec_len, iter_stride, chain0);
 }
 void launch_advance(DevState* ds, int nch, cudaStream_t s) { k_advance<<<nch, 1, 0, s>>>(ds); }
+void launch_commit_data(DevState* ds, const double* part, long long cstride, int nblk, int slot, int nch,
+                        cudaStream_t s) {
+  k_commit_data<<<nch, 256, 0, s>>>(ds, part, cstride, nblk, slot);
+}
 void launch_reset_rec(DevState* ds, int nch, cudaStream_t s) { k_reset_rec<<<nch, 1, 0, s>>>(ds); }
 void launch_zero_dc(float2* spec, cudaStream_t s) { k_zero_dc<<<1, 1, 0, s>>>(spec); }
 void launch_mstat(const ScalarArgs& a, int region, int nblk, int n_mass, int final_, int nch, cudaStream_t s) {

@@ -90,6 +90,11 @@ void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, doub
 void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long iter_stride, int chain0, int nch,
                    cudaStream_t s);
 void launch_advance(DevState* ds, int nch, cudaStream_t s);
+// activate an uploaded survey: data constants from the data kernel's partials
+// (4 x nblk per subsample, chains cstride apart) and DevState::dslot = slot, or
+// ST_BADDATA for invalid data
+void launch_commit_data(DevState* ds, const double* part, long long cstride, int nblk, int slot, int nch,
+                        cudaStream_t s);
 void launch_reset_rec(DevState* ds, int nch, cudaStream_t s);
 // per mass bin j < n_mass: DevState::mstat[j] += (or mstat2[j] =, when `final`) the sum of partials
 void launch_mstat(const ScalarArgs& a, int region, int nblk, int n_mass, int final_, int nch, cudaStream_t s);

@@ -547,10 +547,11 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   // zero force, written without reading W, or zero sums.
   constexpr bool SUPPORT = MODE == Z_GRAD || MODE == Z_SUMS;
   __shared__ int s_lo[SUPPORT ? LINES : 1], s_hi[SUPPORT ? LINES : 1];
+  const SurveyData sd = survey(fp);
   if constexpr (SUPPORT) {
     if (t < LINES) {
-      if (fp.span) {
-        const int2 sp = fp.span[L0 + t];
+      if (sd.span) {
+        const int2 sp = sd.span[L0 + t];
         s_lo[t] = N - sp.x;
         s_hi[t] = sp.y;
       } else {
@@ -690,8 +691,8 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       for (int l = 0; l < nsub; ++l) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (f < LP) {
-          const uint16_t* cn = fp.cnt + l * nv;
-          const float* rr = fp.R + l * nv;
+          const uint16_t* cn = sd.cnt + l * nv;
+          const float* rr = sd.R + l * nv;
 #pragma unroll
           for (int d = 0; d < R2; ++d) {
             const int n = c + R1 * d;
@@ -798,17 +799,18 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
   float acc = 0.f, comp = 0.f;   // FP32 with Kahan compensation per thread; FP64 across the block
   const long long n4 = nv / 4;
   const int n_grid = fp.grid_n;
+  const SurveyData sd = survey(fp);
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
-    if (fp.span) {
+    if (sd.span) {
       const long long line = (4 * i) / n_grid;
       const int z = (int)(4 * i - line * n_grid);
-      const int2 sp = fp.span[line];
+      const int2 sp = sd.span[line];
       if (z < n_grid - sp.x || z >= sp.y) continue;
     }
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Cc = A;
     for (int l = 0; l < nsub; ++l) {
-      const float4 r = reinterpret_cast<const float4*>(fp.R + l * nv)[i];
-      const ushort4 n = reinterpret_cast<const ushort4*>(fp.cnt + l * nv)[i];
+      const float4 r = reinterpret_cast<const float4*>(sd.R + l * nv)[i];
+      const ushort4 n = reinterpret_cast<const ushort4*>(sd.cnt + l * nv)[i];
       const float ka = s_a[l], kb = s_b[l], kbn = s_bn[l];
       A.x = fmaf(ka, r.x, A.x); A.y = fmaf(ka, r.y, A.y); A.z = fmaf(ka, r.z, A.z); A.w = fmaf(ka, r.w, A.w);
       Cc.x += kb * (float)n.x - kbn * r.x;
@@ -825,7 +827,8 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
 }
 
 // Data check and compression: counts int32 -> uint16, R copied; per block the
-// sums R, N^2/R, #(R>0) over R > 0 and the number of invalid voxels.  Per
+// sums R, N^2/R, #(R>0) over R > 0 and the number of invalid voxels.  With
+// cout = rout = NULL it only checks (data already in place).  Per
 // thread the sums run in FP32 with Kahan compensation and the counts in
 // integers (FP64 arithmetic is slow on this part); blocks combine in FP64.
 //
@@ -857,8 +860,8 @@ __global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, u
         atomicMax(&span[line].y, hi);
       }
     }
-    cout[i] = (uint16_t)(nok ? n : 0);
-    rout[i] = rok ? r : 0.f;
+    if (cout) cout[i] = (uint16_t)(nok ? n : 0);
+    if (rout) rout[i] = rok ? r : 0.f;
     if (rok && r > 0.f) {
       kahan_add(sR, cR, r);
       const float fn = (float)(nok ? n : 0);

@@ -49,7 +49,23 @@ struct Fields {
   long long data_stride;  // elements per chain of counts / response (max subsamples x voxels)
   long long part_cstride; // doubles of partial sums per chain
   long long span_stride;  // lines per chain (N^2)
+  // Two survey-data slots (counts, R, spans), so that the next survey can be
+  // uploaded while the kernels read the current one; slot s of counts and R
+  // starts s * data_slot elements, of the spans s * span_slot lines, after the
+  // pointers above.  DevState::dslot selects the active slot of each chain.
+  long long data_slot, span_slot;
 };
+
+// The survey data of the chain's active slot.
+struct SurveyData {
+  const uint16_t* cnt;
+  const float* R;
+  const int2* span;       // NULL: dense
+};
+__device__ __forceinline__ SurveyData survey(const Fields& fp) {
+  const long long s = fp.ds->dslot;
+  return {fp.cnt + s * fp.data_slot, fp.R + s * fp.data_slot, fp.span ? fp.span + s * fp.span_slot : nullptr};
+}
 
 // The fields of chain `ch` of a batch (blockIdx.y of the field passes).
 __host__ __device__ __forceinline__ Fields at_chain(Fields f, int ch) {

@@ -94,10 +94,11 @@ __global__ void __launch_bounds__(YZ<N, CL>::NT, 2) k_yzpass(Fields fp0, int reg
   // ---- supports [lo, hi) of a and c on the z lines of this CTA (local row i is
   // y = CL i + r); outside them g = 0
   bool mine = false;
+  const int2* span = survey(fp).span;
   for (int i = t; i < M; i += NT) {
     int lo = 0, hi = N;
-    if (fp.span) {
-      const int2 sp = fp.span[(long long)plane * N + CL * i + r];
+    if (span) {
+      const int2 sp = span[(long long)plane * N + CL * i + r];
       lo = N - sp.x;
       hi = sp.y;
     }

@@ -40,3 +40,15 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_version_without_gpu(lib):
     assert lib.bps_version().decode().startswith("bps")
+
+
+def test_staged_upload_takes_the_callers_arrays_unconverted():
+    # the library copies the caller's memory after the call returns, so the
+    # binding must not hand it a temporary conversion
+    import numpy as np
+
+    from paper_1306_1821_gb300 import bps
+    ok_c, ok_r = np.zeros(8, np.uint16), np.zeros(8, np.float32)
+    for c, r in ((np.zeros(8, np.int32), ok_r), (ok_c, np.zeros(8, np.float64)), (ok_c, np.zeros(16, np.float32)[::2])):
+        with pytest.raises(TypeError):
+            bps.bps_stage_data_host_u16(None, c, r)
