@@ -437,7 +437,9 @@ bps_status bias_stage(bps_ctx* ctx, bool advance) {
 }
 
 // force evaluation of the jump at the current theta (scales js on the device)
-bps_status jump_gradient(bps_ctx* ctx) {
+// One gradient evaluation of the jump's HMC at the current theta, followed by
+// the leapfrog update of `kind` (the reduction and the update share a launch).
+bps_status jump_gradient(bps_ctx* ctx, int kind) {
   Fields f = fields(ctx);
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
@@ -447,8 +449,8 @@ bps_status jump_gradient(bps_ctx* ctx) {
   bps_status sf = force_stage(ctx, f, region_offset(ctx, RG_JLIK), false, s);
   if (sf != BPS_OK) return sf;
   P.x_jgrad(f, region_offset(ctx, RG_JGRAD), B, s);
-  launch_jump_reduce(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), lik_tiles(ctx), B,
-                     s);
+  launch_jump_step(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), lik_tiles(ctx), kind,
+                   B, s);
   LAUNCHED(ctx, 3);
   return BPS_OK;
 }
@@ -462,15 +464,11 @@ bps_status jump_stage(bps_ctx* ctx, bool advance) {
   launch_jump_begin(sa, B, s);
   LAUNCHED(ctx, 1);
   const int L = ctx->cfg.jump_leapfrog;
-  st = jump_gradient(ctx);
+  st = jump_gradient(ctx, J_FIRST);
   if (st != BPS_OK) return st;
-  launch_jump_update(sa, J_FIRST, B, s);
-  LAUNCHED(ctx, 1);
   for (int k = 0; k < L; ++k) {
-    st = jump_gradient(ctx);
+    st = jump_gradient(ctx, k == L - 1 ? J_LAST : J_MID);
     if (st != BPS_OK) return st;
-    launch_jump_update(sa, k == L - 1 ? J_LAST : J_MID, B, s);
-    LAUNCHED(ctx, 1);
   }
   Fields f = fields(ctx);
   ctx->pt.x_scale(f, B, s);   // delta_k <- sqrt(P'/P) delta_k if accepted (Eq. det_trans)

@@ -255,7 +255,8 @@ struct DevState {
   // jump move
   double th[MAXB], rho[MAXB], mu[MAXB], jscale[MAXB], jgrad[MAXB];
   double jeps, ju_acc, jH0, jH1, jdH, jlik;
-  int jaccepted, pad1;
+  int jaccepted;
+  int jdone;                         // blocks of the running jump step that finished (k_jump_step)
   // reductions handed between kernels
   double sigma[MAXB], sums[MAXS][3];
   double lik0, lik1;

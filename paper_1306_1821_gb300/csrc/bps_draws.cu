@@ -291,14 +291,17 @@ __global__ void k_abar(ScalarArgs a0, int region, int nblk) {
 __global__ void k_commit_data(DevState* ds0, const double* part0, long long cstride, int nblk, int slot) {
   DevState* ds = ds0 + blockIdx.x;
   const double* part = part0 + blockIdx.x * cstride;
-  __shared__ double sh[32];
   __shared__ double s_v[MAXS][4];
   const int nsub = ds->nsub;
-  for (int l = 0; l < nsub; ++l)
-    for (int q = 0; q < 4; ++q) {
-      const double v = sum_partials(part + ((size_t)l * 4 + q) * nblk, nblk, sh);
-      if (threadIdx.x == 0) s_v[l][q] = v;
-    }
+  // one warp per quantity (4 per subsample), lanes strided over the partials
+  const int lane = threadIdx.x & 31;
+  for (int q = threadIdx.x >> 5; q < 4 * nsub; q += blockDim.x >> 5) {
+    double v = 0.0;
+    for (int i = lane; i < nblk; i += 32) v += part[(size_t)q * nblk + i];
+    v = warp_sum(v);
+    if (lane == 0) s_v[q >> 2][q & 3] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     bool ok = true;
     for (int l = 0; l < nsub; ++l) ok = ok && s_v[l][3] == 0.0 && s_v[l][2] > 0.0;
@@ -342,32 +345,19 @@ __global__ void k_jump_begin(ScalarArgs a0) {
   }
 }
 
-// blocks m < n_bins: gradient d psi_J / d theta_m = (alpha - 1) + (1/2N^3) sum_{k in m} w Re(conj(g) delta);
-// block n_bins: likelihood energy at theta
-__global__ void k_jump_reduce(ScalarArgs a0, int r_grad, int nx, int r_lik, int nz) {
-  const ScalarArgs a = chain_args(a0, blockIdx.y);
-  __shared__ double sh[32];
+// Leapfrog update of the jump's HMC in theta after a gradient evaluation (kind:
+// J_FIRST half kick and drift with the starting energy, J_MID kick and drift,
+// J_LAST half kick, final energy and Metropolis test).  Threads m < n_bins own
+// bin m; every thread of the block takes part in the barriers.
+__device__ void jump_update(const ScalarArgs& a, int kind, double* sh) {
   DevState* ds = a.ds;
-  const int m = blockIdx.x;
-  if (m < a.n_bins) {
-    const double s = sum_partials(a.part + r_grad + (size_t)m * a.stride, nx, sh);
-    if (threadIdx.x == 0) ds->jgrad[m] = (a.alpha - 1.0) + 0.5 * a.inv_nv * s;
-  } else {
-    const double s = sum_partials(a.part + r_lik, nz, sh);
-    if (threadIdx.x == 0) ds->jlik = s;
-  }
-}
-
-__global__ void k_jump_update(ScalarArgs a0, int kind) {
-  const ScalarArgs a = chain_args(a0, blockIdx.y);
-  __shared__ double sh[32];
-  DevState* ds = a.ds;
-  const int m = threadIdx.x;   // 64 threads
+  const int m = threadIdx.x;
   const double eps = ds->jeps;
   const bool act = m < a.n_bins;
   double kin = 0.0, pri = 0.0;
   double rho = act ? ds->rho[m] : 0.0, th = act ? ds->th[m] : 0.0;
-  const double mu = act ? ds->mu[m] : 1.0, g = act ? ds->jgrad[m] : 0.0;
+  // written by the other blocks of this launch: read past L1
+  const double mu = act ? ds->mu[m] : 1.0, g = act ? __ldcg(&ds->jgrad[m]) : 0.0;
   if (kind == J_FIRST && act) {
     kin = 0.5 * rho * rho / mu;
     pri = (a.alpha - 1.0) * th;
@@ -385,19 +375,21 @@ __global__ void k_jump_update(ScalarArgs a0, int kind) {
   double e = kin + pri;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  __syncthreads();
   if ((m & 31) == 0) sh[m >> 5] = e;
   __syncthreads();
-  const double E = sh[0] + sh[1];
+  const double E = sh[0] + sh[1];   // bins live in the first two warps (n_bins <= 64)
   if (act) {
     ds->rho[m] = rho;
     ds->th[m] = th;
     ds->js[m] = (float)sqrt(exp(th) / ds->P[m]);
   }
-  if (kind == J_FIRST && m == 0) ds->jH0 = E + ds->jlik;
+  const double jlik = __ldcg(&ds->jlik);
+  if (kind == J_FIRST && m == 0) ds->jH0 = E + jlik;
   if (kind == J_LAST) {
     __shared__ int s_acc;
     if (m == 0) {
-      const double H1 = E + ds->jlik;
+      const double H1 = E + jlik;
       const double dH = H1 - ds->jH0;
       ds->jH1 = H1;
       ds->jdH = dH;
@@ -410,6 +402,36 @@ __global__ void k_jump_update(ScalarArgs a0, int kind) {
     __syncthreads();
     if (act && s_acc) ds->P[m] = exp(th);
   }
+}
+
+
+// One leapfrog step of the jump after its gradient evaluation, in one launch:
+// blocks m < n_bins reduce the gradient d psi_J / d theta_m = (alpha - 1) +
+// (1/2N^3) sum_{k in m} w Re(conj(g) delta), block n_bins the likelihood energy
+// at theta; the last block to finish (a counter in the chain state, which it
+// resets) then applies the update of `kind`.
+__global__ void k_jump_step(ScalarArgs a0, int r_grad, int nx, int r_lik, int nz, int kind) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
+  __shared__ double sh[32];
+  __shared__ int s_last;
+  DevState* ds = a.ds;
+  const int m = blockIdx.x;
+  if (m < a.n_bins) {
+    const double s = sum_partials(a.part + r_grad + (size_t)m * a.stride, nx, sh);
+    if (threadIdx.x == 0) ds->jgrad[m] = (a.alpha - 1.0) + 0.5 * a.inv_nv * s;
+  } else {
+    const double s = sum_partials(a.part + r_lik, nz, sh);
+    if (threadIdx.x == 0) ds->jlik = s;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ds->jdone, 1) == a.n_bins;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) ds->jdone = 0;
+  jump_update(a, kind, sh);
 }
 
 // ------------------------------------------------------------------ misc
@@ -474,11 +496,9 @@ void launch_abar(const ScalarArgs& a, int region, int nblk, int nch, cudaStream_
   k_abar<<<dim3(1, nch), 256, 0, s>>>(a, region, nblk);
 }
 void launch_jump_begin(const ScalarArgs& a, int nch, cudaStream_t s) { k_jump_begin<<<dim3(1, nch), MAXB, 0, s>>>(a); }
-void launch_jump_reduce(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, int nch, cudaStream_t s) {
-  k_jump_reduce<<<dim3(a.n_bins + 1, nch), 256, 0, s>>>(a, r_grad, nx, r_lik, nz);
-}
-void launch_jump_update(const ScalarArgs& a, int kind, int nch, cudaStream_t s) {
-  k_jump_update<<<dim3(1, nch), MAXB, 0, s>>>(a, kind);
+void launch_jump_step(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, int kind, int nch,
+                      cudaStream_t s) {
+  k_jump_step<<<dim3(a.n_bins + 1, nch), 256, 0, s>>>(a, r_grad, nx, r_lik, nz, kind);
 }
 void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, double scale, double* out_dev,
                       cudaStream_t s) {
@@ -491,7 +511,7 @@ void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long 
 void launch_advance(DevState* ds, int nch, cudaStream_t s) { k_advance<<<nch, 1, 0, s>>>(ds); }
 void launch_commit_data(DevState* ds, const double* part, long long cstride, int nblk, int slot, int nch,
                         cudaStream_t s) {
-  k_commit_data<<<nch, 256, 0, s>>>(ds, part, cstride, nblk, slot);
+  k_commit_data<<<nch, 1024, 0, s>>>(ds, part, cstride, nblk, slot);
 }
 void launch_reset_rec(DevState* ds, int nch, cudaStream_t s) { k_reset_rec<<<nch, 1, 0, s>>>(ds); }
 void launch_zero_dc(float2* spec, cudaStream_t s) { k_zero_dc<<<1, 1, 0, s>>>(spec); }
