@@ -72,13 +72,34 @@ __device__ __forceinline__ const float2* buf_ptr(const Fields& fp, int b) {
 #ifndef BPS_XPASS_MIN_BLOCKS
 #define BPS_XPASS_MIN_BLOCKS 2
 #endif
+// the leapfrog x pass works through its column in BPS_XLEAP_CHUNKS parts, so
+// that BPS_XLEAP_MIN_BLOCKS CTAs of 256 threads fit on an SM without spills
+#ifndef BPS_XLEAP_MIN_BLOCKS
+#define BPS_XLEAP_MIN_BLOCKS 3
+#endif
+#ifndef BPS_XLEAP_CHUNKS
+#define BPS_XLEAP_CHUNKS 4
+#endif
+// the jump's inverse x pass and its gradient fit four CTAs per SM (64 registers)
+// without spills
+#ifndef BPS_XJINV_MIN_BLOCKS
+#define BPS_XJINV_MIN_BLOCKS 4
+#endif
+#ifndef BPS_XJGRAD_MIN_BLOCKS
+#define BPS_XJGRAD_MIN_BLOCKS 4
+#endif
+// the y passes fit four CTAs per SM (64 registers) without spills
 #ifndef BPS_YPASS_MIN_BLOCKS
-#define BPS_YPASS_MIN_BLOCKS 1
+#define BPS_YPASS_MIN_BLOCKS 4
 #endif
 
 // ------------------------------------------------------------------ x pass
 template <int N, int MODE>
-__global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fields fp0, XArgs xa) {
+__global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_BLOCKS
+                                              : MODE == X_JINV  ? BPS_XJINV_MIN_BLOCKS
+                                              : MODE == X_JGRAD ? BPS_XJGRAD_MIN_BLOCKS
+                                                                : BPS_XPASS_MIN_BLOCKS)
+    k_xpass(Fields fp0, XArgs xa) {
   const Fields fp = at_chain(fp0, blockIdx.y);
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT, NW = NT / 32;
@@ -206,20 +227,26 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
     float2* dst = dsel(fp, 1 - cur);
     const float eps = (float)ds->eps;
     const float ek = xa.first ? 0.5f * eps : eps;
-    float2 x[R1], p[R1];
+    // the column in parts: the loads of a part in flight together, at a
+    // fraction of the registers of a whole column
+    constexpr int HALF = R1 / BPS_XLEAP_CHUNKS > 0 ? R1 / BPS_XLEAP_CHUNKS : 1;
     if (act) {
 #pragma unroll
-      for (int d = 0; d < R1; ++d) {
-        const long long idx = colo + (long long)(jc + R2 * d) * T.rs;
-        x[d] = src[idx];
-        p[d] = fp.ph[idx];
+      for (int h = 0; h < R1; h += HALF) {
+      float2 x[HALF], p[HALF];
+#pragma unroll
+      for (int q = 0; q < HALF; ++q) {
+        const long long idx = colo + (long long)(jc + R2 * (h + q)) * T.rs;
+        x[q] = src[idx];
+        p[q] = fp.ph[idx];
       }
 #pragma unroll
-      for (int d = 0; d < R1; ++d) {
+      for (int q = 0; q < HALF; ++q) {
+        const int d = h + q;
         const int k = jc + R2 * d;
         float il, im, sm;
         const int m = mode_bin(k, il, im, sm);
-        float2 xx = x[d], pp = p[d];
+        float2 xx = x[q], pp = p[q];
         if (m >= 0) {
           const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
           pp.x = fmaf(-ek, gx, pp.x);
@@ -235,6 +262,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XPASS_MIN_BLOCKS) k_xpass(Fiel
         fp.ph[idx] = pp;
         dst[idx] = xx;
         v[d] = xx;
+      }
       }
     }
     fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
