@@ -96,9 +96,13 @@ bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* c
 /* Survey data (Eq. data_model): counts_dev int32 [n_sub][N][N][N] (galaxy
  * counts N^l_i, 0..65535) and R_dev float32 [n_sub][N][N][N] (survey response
  * R^l_i = C^l_i F^l_i >= 0).  Copied into library buffers; the per-subsample
- * constants sum R, sum N^2/R and N_obs (Sec. 3.6) are computed here.
+ * constants sum R, sum N^2/R and N_obs (Sec. 3.6) are computed here, and so is
+ * the support of each z line (the range of voxels with R > 0 in some
+ * subsample), outside which a = c = 0 and the kernels read no data.  Waits for
+ * the upload and for any survey staged before it (bps_stage_data_host_u16).
  * BPS_EINVAL if R < 0 or non-finite, a count is negative or above 65535, a
- * voxel has R = 0 and a count > 0, or a subsample has no observed voxel. */
+ * voxel has R = 0 and a count > 0, or a subsample has no observed voxel; the
+ * chain then has no data until a valid survey is set. */
 bps_status bps_set_data(bps_ctx* ctx, const int32_t* counts_dev, const float* R_dev);
 
 /* Same as bps_set_data from host arrays (pageable or pinned).  Subsamples are
@@ -107,7 +111,8 @@ bps_status bps_set_data(bps_ctx* ctx, const int32_t* counts_dev, const float* R_
 bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R);
 
 /* Same with the counts as uint16 [n_sub][N][N][N] (the library's own storage
- * width; counts are bounded by 65535 in any case): a quarter less to copy. */
+ * width; counts are bounded by 65535 in any case): a quarter less to copy, and
+ * the arrays are copied straight into the library's buffers and checked there. */
 bps_status bps_set_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R);
 
 /* Starts the upload of a survey (counts uint16 and R float32 [n_sub][N][N][N],

@@ -52,3 +52,27 @@ def test_staged_upload_takes_the_callers_arrays_unconverted():
     for c, r in ((np.zeros(8, np.int32), ok_r), (ok_c, np.zeros(8, np.float64)), (ok_c, np.zeros(16, np.float32)[::2])):
         with pytest.raises(TypeError):
             bps.bps_stage_data_host_u16(None, c, r)
+
+
+def test_z_pass_bytes_counts_the_line_supports():
+    # bench.py's algorithmic bytes of the force z pass, against a direct count:
+    # W read on lines that meet the survey, W written on all lines, a and c over
+    # each line's support [first & ~3, (last + 4) & ~3)
+    import sys
+
+    import numpy as np
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
+    import bench
+    N = 8
+    rng = np.random.default_rng(1)
+    R = np.zeros((2, N, N, N), np.float32)
+    R[0, 1, 2, 3] = 1.0                 # line (1, 2): voxels 3..3 -> [0, 4)
+    R[1, 1, 2, 6] = 0.5                 # same line, other subsample: ... 6 -> [0, 8)
+    R[0, 4, 4, 1:3] = 2.0               # line (4, 4): voxels 1..2 -> [0, 4)
+    R[1, 7, 0, 4:6] = rng.random(2) + 0.1   # line (7, 0): voxels 4..5 -> [4, 8)
+    total, info = bench.z_pass_bytes(R, N)
+    row = (N // 2 + 1) * 8
+    lines, span = 3, 8 + 4 + 4
+    assert total == row * (lines + N * N) + 2 * 4 * span
+    assert info["lines_with_support"] == lines / (N * N)
+    assert info["support_voxels"] == span / N ** 3
