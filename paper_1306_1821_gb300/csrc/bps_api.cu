@@ -455,11 +455,15 @@ bps_status jump_gradient(bps_ctx* ctx, int kind) {
   return BPS_OK;
 }
 
-bps_status jump_stage(bps_ctx* ctx, bool advance) {
+// sigma_current: DevState::sigma already holds the k-bin power of the current
+// field (the power draw of the same Gibbs iteration computed it, and the field
+// has not moved since), so the jump's mass needs no second reduction.
+bps_status jump_stage(bps_ctx* ctx, bool advance, bool sigma_current = false) {
   ScalarArgs sa = scalars(ctx);
   cudaStream_t s = ctx->stream;
   const int B = ctx->batch;
-  bps_status st = power_stage(ctx, false, false);   // sigma of the current field (mass of the jump)
+  bps_status st = BPS_OK;
+  if (!sigma_current) st = power_stage(ctx, false, false);   // sigma of the current field (mass of the jump)
   if (st != BPS_OK) return st;
   launch_jump_begin(sa, B, s);
   LAUNCHED(ctx, 1);
@@ -485,7 +489,7 @@ bps_status jump_stage(bps_ctx* ctx, bool advance) {
 bps_status gibbs_once(bps_ctx* ctx, double* rec, int rec_len, long long iter_stride, bool jump) {
   bps_status st = hmc_move(ctx, false);
   if (st == BPS_OK) st = power_stage(ctx, true, false);
-  if (st == BPS_OK && jump) st = jump_stage(ctx, false);
+  if (st == BPS_OK && jump) st = jump_stage(ctx, false, true);
   if (st == BPS_OK) st = bias_stage(ctx, false);
   if (st != BPS_OK) return st;
   launch_record(scalars(ctx), rec, rec_len, iter_stride, ctx->chain_id.empty() ? 0 : ctx->chain_id[0], ctx->batch,

@@ -825,16 +825,9 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
   }
   __syncthreads();
   float acc = 0.f, comp = 0.f;   // FP32 with Kahan compensation per thread; FP64 across the block
-  const long long n4 = nv / 4;
-  const int n_grid = fp.grid_n;
   const SurveyData sd = survey(fp);
-  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
-    if (sd.span) {
-      const long long line = (4 * i) / n_grid;
-      const int z = (int)(4 * i - line * n_grid);
-      const int2 sp = sd.span[line];
-      if (z < n_grid - sp.x || z >= sp.y) continue;
-    }
+  // a and c of the four voxels of float4 group i
+  auto group = [&](long long i) -> float {
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Cc = A;
     for (int l = 0; l < nsub; ++l) {
       const float4 r = reinterpret_cast<const float4*>(sd.R + l * nv)[i];
@@ -848,7 +841,22 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
     }
     reinterpret_cast<float4*>(fp.a)[i] = A;
     reinterpret_cast<float4*>(fp.c)[i] = Cc;
-    kahan_add(acc, comp, (A.x + A.y) + (A.z + A.w));
+    return (A.x + A.y) + (A.z + A.w);
+  };
+  if (sd.span) {
+    // one warp per z line, its lanes over the line's support (multiples of 4 voxels)
+    const int n_grid = fp.grid_n;
+    const int lines = n_grid * n_grid, gpl = n_grid / 4;   // float4 groups per line
+    const int lane = threadIdx.x & 31;
+    for (int line = blockIdx.x * 8 + (threadIdx.x >> 5); line < lines; line += gridDim.x * 8) {
+      const int2 sp = sd.span[line];
+      const int g0 = (n_grid - sp.x) / 4, g1 = sp.y / 4;
+      for (int g = g0 + lane; g < g1; g += 32) kahan_add(acc, comp, group((long long)line * gpl + g));
+    }
+  } else {
+    const long long n4 = nv / 4;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256)
+      kahan_add(acc, comp, group(i));
   }
   double s = block_sum<256>((double)acc - (double)comp, s_red);
   if (threadIdx.x == 0) fp.part[region + blockIdx.x] = s;
@@ -880,8 +888,9 @@ __global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, u
     if (span) {
       const unsigned m = __ballot_sync(0xffffffffu, rok && r > 0.f);
       if (m != 0u && (threadIdx.x & 31) == 0) {
-        const long long line = i / n_grid;
-        const int z0 = (int)(i - line * n_grid);
+        const int ii = (int)i;                 // < N^3 <= 512^3: 32-bit division
+        const int line = ii / n_grid;
+        const int z0 = ii - line * n_grid;
         const int lo = (z0 + __ffs((int)m) - 1) & ~3;
         const int hi = (z0 + 32 - __clz((int)m) + 3) & ~3;
         atomicMax(&span[line].x, n_grid - lo);
