@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (FP32 fields against FP64, derived in the design doc):
+Tolerances (FP32 fields against FP64, from the FP32 rounding of each step):
   * 3D transforms: relative L2 <= 2e-6 (FP32 rounding of log2(N^3) butterfly stages);
   * force (Eq. Wiener_Posterior_force): relative L2 <= 1e-5;
   * HMC move: |dH_gpu - dH_oracle| <= 1e-3 and the same Metropolis decision unless
