@@ -381,3 +381,40 @@ def test_step_size_adaptation_moves_acceptance_toward_target(torch_cuda):
             bps.bps_adapt_step_size(s.ctx, 1, 1, 1.5)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("fused", ["0", "1"])
+def test_line_supports_at_the_ends_of_the_lines(torch_cuda, monkeypatch, fused):
+    """Supports are rounded to multiples of four voxels: single observed voxels at
+    z = 0 and z = N - 1, a fully observed line, a short run in the middle of a
+    line and observed voxels in only one of two subsamples must all reach the force
+    and the likelihood energy (three passes and the fused plane kernel)."""
+    from paper_1306_1821_gb300 import bps
+    monkeypatch.setenv("BPS_FUSED_YZ", fused)
+    torch = torch_cuda
+    N = 32
+    pb = Problem(N, n_sub=2, n_bins=4)
+    R = np.zeros_like(pb.R)
+    counts = np.zeros_like(pb.counts)
+    spots = [(0, 3, 5, 0), (0, 3, 6, N - 1), (1, 10, 1, 0), (1, 10, 1, N - 1), (0, 20, 20, 13),
+             (1, 31, 0, 17), (0, 31, 31, N - 1)]
+    for l, x, y, z in spots:
+        R[l, x, y, z] = 0.8
+        counts[l, x, y, z] = 2
+    R[0, 7, 7, :] = 0.5                         # a fully observed line
+    counts[0, 7, 7, ::3] = 1
+    R[1, 12, 4, 9:14] = 1.2                     # a run inside one line
+    counts[1, 12, 4, 10] = 4
+    s = bps.Sampler(N, pb.wl.box, 2, pb.wl.n_bins, **pb.config_kwargs(11))
+    try:
+        bps.bps_set_data(s.ctx, torch.from_numpy(counts).cuda(), torch.from_numpy(R).cuda())
+        bps.bps_set_state(s.ctx, None, pb.P, pb.b, pb.nbar, 0)
+        bps.bps_set_spectrum(s.ctx, torch.from_numpy(pb.dh32).cuda())
+        g = torch.zeros((N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+        e = bps.bps_gradient(s.ctx, g)
+        a, c = model.local_fields(counts, R, pb.b, pb.nbar)
+        gh, lik = model.gradient_hat(pb.geom, pb.dh, pb.P, a, c)
+        assert rel_l2(g.cpu().numpy(), gh) < 1e-5
+        assert abs(e[1] - lik) < 1e-5 * (abs(lik) + np.sum(np.abs(a * grid.inverse(pb.dh, N) ** 2)))
+    finally:
+        s.close()
