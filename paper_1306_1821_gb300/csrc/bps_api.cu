@@ -283,6 +283,13 @@ bps_status check_status(bps_ctx* ctx) {
       int zero = 0;
       ds_write_bytes(ctx, ch, DS_OFF(status), &zero, sizeof(int));
       any |= st;
+      if (st & ST_BADDATA) {
+        // a chain whose surveys were all invalid has none: only a valid commit
+        // writes the observed-voxel counts
+        double nobs0 = 0.0;
+        if (ds_read_bytes(ctx, ch, DS_OFF(nobs), &nobs0, sizeof(double)) == BPS_OK && !(nobs0 > 0.0))
+          ctx->have_data[ch] = 0;
+      }
     }
   }
   if (any & ST_BADDATA)

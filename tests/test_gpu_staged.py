@@ -131,3 +131,30 @@ def test_invalid_staged_survey_keeps_the_previous_one(torch_cuda):
     finally:
         ref.close()
         s.close()
+
+
+def test_invalid_first_survey_leaves_no_data(torch_cuda):
+    """A context whose only staged survey is invalid has no data afterwards: the
+    activating call reports the data error, later calls report missing data, and a
+    valid survey makes the chain usable."""
+    from paper_1306_1821_gb300 import bps
+    torch = torch_cuda
+    pb = Problem(32, n_sub=1, n_bins=4)
+    s = fresh(pb, 3)
+    try:
+        bad = pb.counts.copy()
+        bad[0].flat[np.flatnonzero(pb.R[0] == 0)[0]] = 1          # a count where R = 0
+        c, r = pinned(torch, bad, np.uint16), pinned(torch, pb.R, np.float32)
+        bps.bps_stage_data_host_u16(s.ctx, c, r)
+        start_state(s, pb)
+        with pytest.raises(bps.BpsError) as e:
+            bps.bps_gibbs_iterate(s.ctx, 1, s.rec_len)
+        assert e.value.status == bps.BPS_EINVAL
+        with pytest.raises(bps.BpsError) as e:
+            bps.bps_gibbs_iterate(s.ctx, 1, s.rec_len)
+        assert e.value.status == bps.BPS_ESTATE
+        bps.bps_set_data_host_u16(s.ctx, pinned(torch, pb.counts, np.uint16), r)
+        start_state(s, pb)
+        assert np.all(np.isfinite(bps.bps_gibbs_iterate(s.ctx, 1, s.rec_len)))
+    finally:
+        s.close()
