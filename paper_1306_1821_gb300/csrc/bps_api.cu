@@ -456,8 +456,8 @@ bps_status jump_gradient(bps_ctx* ctx, int kind) {
   bps_status sf = force_stage(ctx, f, region_offset(ctx, RG_JLIK), false, s);
   if (sf != BPS_OK) return sf;
   P.x_jgrad(f, region_offset(ctx, RG_JGRAD), B, s);
-  launch_jump_step(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK), lik_tiles(ctx), kind,
-                   B, s);
+  launch_jump_step(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK),
+                   region_offset(ctx, RG_LIK1), lik_tiles(ctx), kind, B, s);
   LAUNCHED(ctx, 3);
   return BPS_OK;
 }
@@ -472,7 +472,9 @@ bps_status jump_stage(bps_ctx* ctx, bool advance, bool sigma_current = false) {
   bps_status st = BPS_OK;
   if (!sigma_current) st = power_stage(ctx, false, false);   // sigma of the current field (mass of the jump)
   if (st != BPS_OK) return st;
-  launch_jump_begin(sa, B, s);
+  // inside the Gibbs scan the jump follows the HMC move and the power draw, which
+  // leave W and the likelihood partials of the move's last force evaluation
+  launch_jump_begin(sa, sigma_current ? 1 : 0, B, s);
   LAUNCHED(ctx, 1);
   const int L = ctx->cfg.jump_leapfrog;
   st = jump_gradient(ctx, J_FIRST);

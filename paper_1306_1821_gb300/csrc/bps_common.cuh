@@ -257,6 +257,10 @@ struct DevState {
   double jeps, ju_acc, jH0, jH1, jdH, jlik;
   int jaccepted;
   int jdone;                         // blocks of the running jump step that finished (k_jump_step)
+  // 1 while the jump's first gradient can reuse the force of the HMC move just
+  // accepted (W and the likelihood partials of its last force evaluation are
+  // those of the current field): its force stage is skipped
+  int jreuse, pad1;
   // reductions handed between kernels
   double sigma[MAXB], sums[MAXS][3];
   double lik0, lik1;

@@ -322,12 +322,15 @@ __global__ void k_commit_data(DevState* ds0, const double* part0, long long cstr
 // HMC in theta = ln P with the whitened field fixed (Sec. 4.3, App. C).
 // Mass mu_m = max(1, abar P_ref_m sigma_m / (4 V_cell P_m)): built from the
 // whitened field and a fixed reference spectrum, never from the current P.
-__global__ void k_jump_begin(ScalarArgs a0) {
+// reuse: the jump directly follows this iteration's HMC move and power draw, so
+// after an accepted move the first gradient can take the move's last force.
+__global__ void k_jump_begin(ScalarArgs a0, int reuse) {
   const ScalarArgs a = chain_args(a0, blockIdx.y);
   DevState* ds = a.ds;
   const int m = threadIdx.x;
   const uint64_t it = ds->iteration;
   if (m == 0) {
+    ds->jreuse = reuse && ds->accepted;
     P4 r = philox(0, it, ST_JUMP, 0, ds->seed);
     ds->jeps = a.jeps_max * u52(r.w[0]);
     ds->ju_acc = u52(r.w[1]);
@@ -410,7 +413,7 @@ __device__ void jump_update(const ScalarArgs& a, int kind, double* sh) {
 // (1/2N^3) sum_{k in m} w Re(conj(g) delta), block n_bins the likelihood energy
 // at theta; the last block to finish (a counter in the chain state, which it
 // resets) then applies the update of `kind`.
-__global__ void k_jump_step(ScalarArgs a0, int r_grad, int nx, int r_lik, int nz, int kind) {
+__global__ void k_jump_step(ScalarArgs a0, int r_grad, int nx, int r_lik, int r_lik_move, int nz, int kind) {
   const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
   __shared__ int s_last;
@@ -420,7 +423,8 @@ __global__ void k_jump_step(ScalarArgs a0, int r_grad, int nx, int r_lik, int nz
     const double s = sum_partials(a.part + r_grad + (size_t)m * a.stride, nx, sh);
     if (threadIdx.x == 0) ds->jgrad[m] = (a.alpha - 1.0) + 0.5 * a.inv_nv * s;
   } else {
-    const double s = sum_partials(a.part + r_lik, nz, sh);
+    // a reused force stage left its likelihood partials where the move's last one wrote them
+    const double s = sum_partials(a.part + (ds->jreuse ? r_lik_move : r_lik), nz, sh);
     if (threadIdx.x == 0) ds->jlik = s;
   }
   if (threadIdx.x == 0) {
@@ -430,7 +434,10 @@ __global__ void k_jump_step(ScalarArgs a0, int r_grad, int nx, int r_lik, int nz
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x == 0) ds->jdone = 0;
+  if (threadIdx.x == 0) {
+    ds->jdone = 0;
+    ds->jreuse = 0;               // only the first gradient can reuse the move's force
+  }
   jump_update(a, kind, sh);
 }
 
@@ -495,10 +502,12 @@ void launch_bias_nbar(const ScalarArgs& a, int region, int nz, int nch, cudaStre
 void launch_abar(const ScalarArgs& a, int region, int nblk, int nch, cudaStream_t s) {
   k_abar<<<dim3(1, nch), 256, 0, s>>>(a, region, nblk);
 }
-void launch_jump_begin(const ScalarArgs& a, int nch, cudaStream_t s) { k_jump_begin<<<dim3(1, nch), MAXB, 0, s>>>(a); }
-void launch_jump_step(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, int kind, int nch,
-                      cudaStream_t s) {
-  k_jump_step<<<dim3(a.n_bins + 1, nch), 256, 0, s>>>(a, r_grad, nx, r_lik, nz, kind);
+void launch_jump_begin(const ScalarArgs& a, int reuse, int nch, cudaStream_t s) {
+  k_jump_begin<<<dim3(1, nch), MAXB, 0, s>>>(a, reuse);
+}
+void launch_jump_step(const ScalarArgs& a, int r_grad, int nx, int r_lik, int r_lik_move, int nz, int kind,
+                      int nch, cudaStream_t s) {
+  k_jump_step<<<dim3(a.n_bins + 1, nch), 256, 0, s>>>(a, r_grad, nx, r_lik, r_lik_move, nz, kind);
 }
 void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, double scale, double* out_dev,
                       cudaStream_t s) {

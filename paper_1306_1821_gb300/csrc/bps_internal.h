@@ -82,10 +82,11 @@ void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, i
 void launch_power(const ScalarArgs& a, int region, int nx, int draw, int nch, cudaStream_t s);
 void launch_bias_nbar(const ScalarArgs& a, int region, int nz, int nch, cudaStream_t s);
 void launch_abar(const ScalarArgs& a, int region, int nblk, int nch, cudaStream_t s);
-void launch_jump_begin(const ScalarArgs& a, int nch, cudaStream_t s);
+// reuse = 1: after an accepted HMC move the first gradient takes the move's last force stage
+void launch_jump_begin(const ScalarArgs& a, int reuse, int nch, cudaStream_t s);
 // reduce the jump gradient and likelihood partials, then the leapfrog update of `kind` (one launch)
-void launch_jump_step(const ScalarArgs& a, int r_grad, int nx, int r_lik, int nz, int kind, int nch,
-                      cudaStream_t s);
+void launch_jump_step(const ScalarArgs& a, int r_grad, int nx, int r_lik, int r_lik_move, int nz, int kind,
+                      int nch, cudaStream_t s);
 void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, double scale, double* out_dev,
                       cudaStream_t s);
 void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long iter_stride, int chain0, int nch,

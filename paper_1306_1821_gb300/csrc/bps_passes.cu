@@ -117,6 +117,9 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
   if constexpr (MODE == X_SCALE) {
     if (!ds->jaccepted) return;   // uniform across the grid
   }
+  if constexpr (MODE == X_JINV) {
+    if (ds->jreuse) return;       // W already holds this force stage's input (uniform)
+  }
   for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
   for (int i = t; i < MAXB; i += NT) {
     s_thr[i] = ds->thr[i];
@@ -493,6 +496,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
 template <int N, int DIR>
 __global__ void __launch_bounds__(Cfg<N>::NT, BPS_YPASS_MIN_BLOCKS) k_ypass(Fields fp0, int buf) {
   const Fields fp = at_chain(fp0, blockIdx.y);
+  if (buf == BUF_W && fp.ds->jreuse) return;   // force stage reused by the jump (uniform)
   using C = Cfg<N>;
   constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT;
   __shared__ float2 s_tw[N];
@@ -563,6 +567,9 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   const int t = threadIdx.x;
   DevState* ds = fp.ds;
+  if constexpr (MODE == Z_GRAD) {
+    if (ds->jreuse) return;       // force stage reused by the jump (uniform)
+  }
   // Lines in decreasing x: the y passes visit the x planes upwards, so the planes
   // the z pass reads first are the ones the inverse y pass wrote last (still in
   // L2), and the forward y pass starts on the planes the z pass wrote last.

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(YZ<N, CL>::NT, 2) k_yzpass(Fields fp0, int reg
   const int r = CL > 1 ? (int)(blockIdx.x % CL) : 0;     // rank in the cluster (cluster along x)
   const int plane = (int)blockIdx.x / CL;
   DevState* ds = fp.ds;
+  if (ds->jreuse) return;         // force stage reused by the jump (uniform)
   float2* Wp = fp.W + (long long)plane * N * ZP;
 
   // ---- supports [lo, hi) of a and c on the z lines of this CTA (local row i is
