@@ -137,3 +137,47 @@ def test_move_uniforms_follow_counter():
     assert u1 != u2 and all(0 < x < 1 for x in u1 + u2)
     w = philox.words(3, 10, philox.STAGE_HMC, 0, np.zeros(1, dtype=np.uint64))
     assert u1[0] == philox.uniform52(w[0])[0]
+
+
+def test_mass_multipliers_leave_the_closed_form_conditional_unchanged():
+    # Sec. 4.1.2: the mass changes only the efficiency of the move, not its
+    # target.  With R == 1 the conditional of delta is diagonal in Fourier space:
+    # mode k has mean c_hat_k / (1/lambda_k + abar) and full-grid variance
+    # N_vox / (1/lambda_k + abar).  HMC moves under strongly non-uniform mass
+    # multipliers (a function of |n|^2, so the mass stays that of a real field)
+    # must reproduce both.
+    N = 4
+    g = grid.Geometry(N, 200.0, 2)
+    P = np.array([3.0e5, 1.0e5])
+    abar = 2.0
+    a = np.full((N, N, N), abar)
+    rng = np.random.Generator(np.random.PCG64(17))
+    c = rng.standard_normal((N, N, N))
+    il = model.inv_lambda(g, P)
+    q = np.where(g.bin >= 0, il + abar, 1.0)
+    mean_hat = np.where(g.bin >= 0, grid.forward(c) / q, 0.0)
+    var_hat = np.where(g.bin >= 0, g.Nv / q, 0.0)
+    levels = np.unique(g.n2)
+    per_level = dict(zip(levels.tolist(), np.exp(rng.uniform(np.log(1 / 8), np.log(8), len(levels)))))
+    scale = np.vectorize(per_level.get)(g.n2).astype(np.float64)
+    d = mean_hat.copy()
+    n, acc = 6000, 0
+    s1 = np.zeros(d.shape, dtype=np.complex128)
+    s2 = np.zeros(d.shape)
+    for it in range(n):
+        d, info = hmc.hmc_move(g, d, P, a, c, abar, 6, 0.9, 29, it, mass_scale=scale)
+        acc += info["accepted"]
+        s1 += d
+        s2 += np.abs(d - mean_hat) ** 2
+    assert acc / n > 0.6
+    obs = g.bin >= 0
+    # mean: per-mode z-scores against the closed form (moves are close to
+    # independent at this size; allow 4.5 sigma over the modes)
+    z = np.abs(s1 / n - mean_hat)[obs] / np.sqrt(var_hat[obs] / n)
+    assert np.max(z) < 4.5 * np.sqrt(3.0)
+    # variance: the mean ratio over all modes and over each mass level
+    r = (s2 / n)[obs] / var_hat[obs]
+    assert abs(r.mean() - 1.0) < 0.03
+    for lev in levels[levels > 0]:
+        sel = (g.n2 == lev)[obs]
+        assert abs(r[sel].mean() - 1.0) < 0.15, (lev, r[sel].mean())
