@@ -149,6 +149,22 @@ bps_status bps_get_spectrum(bps_ctx* ctx, float* spec_dev);
 /* Replace the current field by a half spectrum (device); k = 0 is zeroed. */
 bps_status bps_set_spectrum(bps_ctx* ctx, const float* spec_dev);
 
+/* Checkpoint and resume of one chain (Sec. 3.2: the state of the multiple-block
+ * scan).  The checkpoint holds the field's half spectrum (its exact FP32 bits),
+ * P, b, Nbar, the jump's reference spectrum (bps_set_state), the iteration
+ * counter of the random streams, eps_max (bps_adapt_step_size may have changed
+ * it) and the mass multipliers of bps_set_mass_scale.  Loaded into a context
+ * created with the same grid, box, subsamples and settings, holding the same
+ * survey, the chain continues bit for bit as if it had not been interrupted.
+ * The survey and a network mass (bps_set_mass_net, bps_set_preconditioner) are
+ * not part of it: set them on the new context first.  bps_save_chain: blob
+ * NULL makes *bytes receive the size needed; otherwise *bytes is the capacity
+ * of blob (host) and receives the size written.  bps_load_chain returns
+ * BPS_EINVAL for a blob of another format, grid, box, subsample or bin count.
+ * Single-chain contexts. */
+bps_status bps_save_chain(bps_ctx* ctx, void* blob, size_t* bytes);
+bps_status bps_load_chain(bps_ctx* ctx, const void* blob, size_t bytes);
+
 /* One HMC move of the density field (Sec. 4.1): momenta drawn afresh
  * (p ~ N(0, M), M diagonal in Fourier space, M_k = V_cell/P_k + abar),
  * n_leapfrog kick-drift-kick steps of size eps_max * u, Metropolis accept in
@@ -348,11 +364,17 @@ bps_status bps_voxel_normals(uint64_t seed, uint64_t iteration, size_t n, float*
  * context is needed.  The caller passes input and output; the library keeps
  * its per-block partial sums in one file-scope device array of 1024 x 64
  * doubles (512 KiB), which every GPU that loads the library holds until the
- * process exits.  Limits: N even in 4..512, 1 <= n_bins <= 64 (BPS_EINVAL
- * beyond them, text in bps_last_error(NULL)).  The first call on each device,
- * with that device current, looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  No call allocates or frees anything.  All calls share the array:
+ * process exits.  Limits: N even in 4..512, 1 <= n_bins <= 64, every bin
+ * holding at least one wave vector of the grid (the bins of bps_create, checked
+ * the same way), spec_dev and sigma_dev 8-byte aligned: BPS_EINVAL otherwise,
+ * text in bps_last_error(NULL).  A CUDA error already pending in the calling
+ * thread is reported as BPS_ECUDA and left pending; nothing is launched.  The
+ * first call on each device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress) in the device's primary context and
+ * caches it; make that first call before any stream capture.  The cache is not
+ * renewed: calls after cudaDeviceReset of that device, or from a non-primary
+ * context, are not supported.  No call allocates or frees anything.  All calls
+ * share the array:
  * calls whose kernels overlap on the GPU (different streams, or other host
  * threads) race and must be serialised by the caller.  Work is queued on
  * cuda_stream (a cudaStream_t, NULL = legacy default stream); the call does not
@@ -377,6 +399,17 @@ uint64_t bps_kernel_launches(const bps_ctx* ctx);
  * read (then resets them).  Timing only; results are unchanged. */
 bps_status bps_profile(bps_ctx* ctx, int enable);
 bps_status bps_profile_read(bps_ctx* ctx, double* ms, uint64_t* n);
+
+/* Self-test of failure detection.  Every device wait of the library (the bulk
+ * tile copies of the z and fused y/z passes complete on shared-memory
+ * mbarriers) is bounded: after 2 s the block gives up, records the timeout in
+ * the chain's status word and exits, and the next call that reads the status
+ * returns BPS_ETIMEOUT with the context still usable.  This call runs that
+ * path on purpose: one block waits on an mbarrier for 16 bytes that no copy
+ * will deliver (none is issued, so nothing is in flight when it gives up),
+ * with the wait limited to limit_ns (1..1e9).  Returns BPS_ETIMEOUT when the
+ * wait ran out as it must; the chain's state is untouched. */
+bps_status bps_selftest_wait(bps_ctx* ctx, uint64_t limit_ns);
 
 /* Line pairs per tile (4, 8 or 16) of the force z pass of ctx (the first
  * group of a batch).  Chosen when the context is created: the first context of

@@ -91,6 +91,9 @@ _SIGS = {
     "bps_set_mass_net": ([_P, _P, _P, _P, ctypes.c_double], ctypes.c_int),
     "bps_get_mass_scale": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D], ctypes.c_int),
     "bps_bin_power_noalloc": ([ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "bps_save_chain": ([_P, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "bps_load_chain": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
+    "bps_selftest_wait": ([_P, ctypes.c_uint64], ctypes.c_int),
     "bps_destroy": ([_P], None),
 }
 
@@ -216,6 +219,24 @@ def bps_get_spectrum(ctx, spec):
 
 def bps_set_spectrum(ctx, spec):
     _check(ctx, load().bps_set_spectrum(ctx, _dptr(spec)))
+
+
+def bps_save_chain(ctx):
+    """Checkpoint of the chain as bytes (the library's format)."""
+    n = ctypes.c_size_t(0)
+    _check(ctx, load().bps_save_chain(ctx, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, load().bps_save_chain(ctx, buf, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def bps_load_chain(ctx, blob):
+    b = bytes(blob)
+    _check(ctx, load().bps_load_chain(ctx, ctypes.c_char_p(b), len(b)))
+
+
+def bps_selftest_wait(ctx, limit_ns):
+    _check(ctx, load().bps_selftest_wait(ctx, int(limit_ns)))
 
 
 def bps_hmc_step(ctx, want_info=True):

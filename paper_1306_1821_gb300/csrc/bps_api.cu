@@ -8,6 +8,7 @@
 // single-chain context is a group of one.  A batch context (bps_create_batch)
 // owns one group per distinct grid size.
 #include <algorithm>
+#include <bitset>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -102,6 +103,85 @@ struct bps_ctx {
   std::string err;
 };
 
+namespace bps {
+
+// ------------------------------------------------------------------ k bins (one definition, shared)
+// bin of integer |n|^2 for n_bins linear bins over (0, sqrt(3) N / 2]
+int bin_of_host(long long n2, int N, int nb) {
+  double b = std::floor((double)nb * std::sqrt((double)n2) / (std::sqrt(3.0) * (double)N / 2.0));
+  int m = (int)b;
+  return m > nb - 1 ? nb - 1 : m;
+}
+
+// thresholds (smallest n2 of each bin) and, when nmodes is given, the full-grid
+// mode counts; false if a bin has no threshold or (with nmodes) no mode
+bool bin_tables(int N, int nb, int* thr, double* nmodes) {
+  for (int m = 0; m < MAXB; ++m) {
+    thr[m] = 0x7fffffff;
+    if (nmodes) nmodes[m] = 0.0;
+  }
+  thr[0] = 0;
+  const long long maxn2 = 3LL * (N / 2) * (N / 2);
+  int prev = 0;
+  for (long long n2 = 1; n2 <= maxn2; ++n2) {
+    int m = bin_of_host(n2, N, nb);
+    while (prev < m) {
+      ++prev;
+      thr[prev] = (int)n2;
+    }
+  }
+  if (nmodes) {
+    const int H = N / 2;
+    for (int ix = 0; ix < N; ++ix) {
+      const long long nx = ix <= H ? ix : ix - N;
+      for (int iy = 0; iy < N; ++iy) {
+        const long long ny = iy <= H ? iy : iy - N;
+        for (int iz = 0; iz <= H; ++iz) {
+          const long long n2 = nx * nx + ny * ny + (long long)iz * iz;
+          if (n2 == 0) continue;
+          const double w = (iz == 0 || iz == H) ? 1.0 : 2.0;
+          nmodes[bin_of_host(n2, N, nb)] += w;
+        }
+      }
+    }
+    for (int m = 0; m < nb; ++m)
+      if (nmodes[m] <= 0.0) return false;
+  }
+  for (int m = 1; m < nb; ++m)
+    if (thr[m] == 0x7fffffff) return false;
+  return true;
+}
+
+
+// true when every bin [thr[m], thr[m+1]) holds at least one integer wave vector
+// of the grid, |n_x|, |n_y|, |n_z| <= N/2 (N <= 512).  Cheaper than counting the
+// modes: a bitmap of the values n_x^2 + n_y^2, then for each bin the first
+// |n|^2 of its range that is such a value plus some n_z^2.  A bin can have
+// thresholds and still no mode (every |n|^2 in it of the form 4^a (8b + 7)).
+bool bins_have_modes(int N, int nb, const int* thr) {
+  constexpr int HMAX = 256;
+  const int H = N / 2;
+  if (H > HMAX || H < 1) return false;
+  std::bitset<2 * HMAX * HMAX + 1> two;   // 16 KB on the stack, nothing allocated
+  for (int x = 0; x <= H; ++x)
+    for (int y = x; y <= H; ++y) two.set((size_t)(x * x + y * y));
+  const long long maxn2 = 3LL * H * H;
+  for (int m = 0; m < nb; ++m) {
+    const long long lo = m == 0 ? 1 : thr[m];
+    const long long hi = m + 1 < nb ? thr[m + 1] : maxn2 + 1;
+    bool found = false;
+    for (long long n2 = lo; n2 < hi && !found; ++n2)
+      for (int z = 0; z <= H && (long long)z * z <= n2 && !found; ++z) {
+        const long long r = n2 - (long long)z * z;
+        if (r <= 2LL * H * H && two.test((size_t)r)) found = true;
+      }
+    if (!found) return false;
+  }
+  return true;
+}
+
+}  // namespace bps
+
 namespace {
 
 std::string g_err;
@@ -110,7 +190,7 @@ std::string g_err;
 enum Region { RG_INIT = 0, RG_LIK0, RG_FINAL, RG_LIK1, RG_BIN, RG_SUMS, RG_RB, RG_JGRAD, RG_JLIK, RG_GRAD, RG_COUNT };
 int region_width(Region r) {
   switch (r) {
-    case RG_INIT: case RG_FINAL: return 2;
+    case RG_INIT: case RG_FINAL: return 3;   // kinetic, prior, g^T M^-1 g
     case RG_BIN: case RG_JGRAD: return MAXB;
     case RG_SUMS: return 3 * MAXS;
     default: return 1;
@@ -208,51 +288,6 @@ ScalarArgs scalars_at(bps_ctx* c, int ch) {
   a.ds += ch;
   a.part += ch * a.cstride;
   return a;
-}
-
-// bin of integer |n|^2 for n_bins linear bins over (0, sqrt(3) N / 2]
-int bin_of_host(long long n2, int N, int nb) {
-  double b = std::floor((double)nb * std::sqrt((double)n2) / (std::sqrt(3.0) * (double)N / 2.0));
-  int m = (int)b;
-  return m > nb - 1 ? nb - 1 : m;
-}
-
-// thresholds (smallest n2 of each bin) and full-grid mode counts; false if a bin is empty
-bool bin_tables(int N, int nb, int* thr, double* nmodes) {
-  for (int m = 0; m < MAXB; ++m) {
-    thr[m] = 0x7fffffff;
-    if (nmodes) nmodes[m] = 0.0;
-  }
-  thr[0] = 0;
-  const long long maxn2 = 3LL * (N / 2) * (N / 2);
-  int prev = 0;
-  for (long long n2 = 1; n2 <= maxn2; ++n2) {
-    int m = bin_of_host(n2, N, nb);
-    while (prev < m) {
-      ++prev;
-      thr[prev] = (int)n2;
-    }
-  }
-  if (nmodes) {
-    const int H = N / 2;
-    for (int ix = 0; ix < N; ++ix) {
-      const long long nx = ix <= H ? ix : ix - N;
-      for (int iy = 0; iy < N; ++iy) {
-        const long long ny = iy <= H ? iy : iy - N;
-        for (int iz = 0; iz <= H; ++iz) {
-          const long long n2 = nx * nx + ny * ny + (long long)iz * iz;
-          if (n2 == 0) continue;
-          const double w = (iz == 0 || iz == H) ? 1.0 : 2.0;
-          nmodes[bin_of_host(n2, N, nb)] += w;
-        }
-      }
-    }
-    for (int m = 0; m < nb; ++m)
-      if (nmodes[m] <= 0.0) return false;
-  }
-  for (int m = 1; m < nb; ++m)
-    if (thr[m] == 0x7fffffff) return false;
-  return true;
 }
 
 #define DS_OFF(member) offsetof(DevState, member)
@@ -391,7 +426,8 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   if (sf != BPS_OK) return sf;
   for (int st = 1; st <= L; ++st) {
     prof_mark(ctx, 0);
-    P.x_leap(f, st == 1 ? 1 : 0, B, s);
+    if (st == 1) P.x_leapg(f, region_offset(ctx, RG_INIT) + 2 * ctx->part_stride, B, s);
+    else P.x_leap(f, 0, B, s);
     prof_mark(ctx, 0);
     sf = force_stage(ctx, f, st == L ? region_offset(ctx, RG_LIK1) : -1, true, s);
     if (sf != BPS_OK) return sf;
@@ -1342,6 +1378,118 @@ bps_status bps_set_spectrum(bps_ctx* ctx, const float* spec_dev) {
   LAUNCHED(ctx, 1);
   CK(cudaStreamSynchronize(ctx->stream));
   return BPS_OK;
+}
+
+// ---- checkpoint of one chain (bps_save_chain / bps_load_chain)
+namespace {
+constexpr char CHAIN_MAGIC[8] = {'B', 'P', 'S', 'C', 'H', 'A', 'I', 'N'};
+struct ChainHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t N, n_sub, n_bins, n_mass, pad;
+  double box, eps_max;
+  uint64_t iteration;
+  double P[MAXB], P_ref[MAXB], b[MAXS], nbar[MAXS], mass_scale[MAXB];
+};
+size_t chain_blob_bytes(const bps_ctx* ctx) {
+  return sizeof(ChainHeader) + (size_t)ctx->N * ctx->N * (ctx->N / 2 + 1) * sizeof(float2);
+}
+}  // namespace
+
+bps_status bps_save_chain(bps_ctx* ctx, void* blob, size_t* bytes) {
+  if (!ctx || ctx->is_batch || !bytes) return fail(ctx, BPS_EINVAL, "null argument or batch context");
+  const size_t need = chain_blob_bytes(ctx);
+  if (!blob) {
+    *bytes = need;
+    return BPS_OK;
+  }
+  if (*bytes < need) return fail(ctx, BPS_EINVAL, "checkpoint buffer too small");
+  ChainHeader h{};
+  std::memcpy(h.magic, CHAIN_MAGIC, 8);
+  h.version = 1;
+  h.N = ctx->N;
+  h.n_sub = ctx->nsub[0];
+  h.n_bins = ctx->cfg.n_bins;
+  h.n_mass = ctx->n_mass;
+  h.box = ctx->box[0];
+  h.eps_max = ctx->cfg.eps_max;
+  unsigned long long it = 0;
+  bps_status st = ds_read_bytes(ctx, 0, DS_OFF(P), h.P, sizeof(h.P));
+  if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(P_ref), h.P_ref, sizeof(h.P_ref));
+  if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(b), h.b, sizeof(h.b));
+  if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(nbar), h.nbar, sizeof(h.nbar));
+  if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(mass_scale), h.mass_scale, sizeof(h.mass_scale));
+  if (st == BPS_OK) st = ds_read_bytes(ctx, 0, DS_OFF(iteration), &it, sizeof(it));
+  if (st != BPS_OK) return st;
+  h.iteration = it;
+  int cur = current_buffer(ctx, 0, &st);
+  if (st != BPS_OK) return st;
+  const size_t H1 = (size_t)ctx->N / 2 + 1;
+  char* out = static_cast<char*>(blob);
+  std::memcpy(out, &h, sizeof h);
+  CK(cudaMemcpy2DAsync(out + sizeof h, H1 * sizeof(float2), ctx->dh[cur], (size_t)ctx->zp * sizeof(float2),
+                       H1 * sizeof(float2), (size_t)ctx->N * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *bytes = need;
+  return BPS_OK;
+}
+
+bps_status bps_load_chain(bps_ctx* ctx, const void* blob, size_t bytes) {
+  if (!ctx || ctx->is_batch || !blob) return fail(ctx, BPS_EINVAL, "null argument or batch context");
+  ChainHeader h;
+  if (bytes < sizeof h) return fail(ctx, BPS_EINVAL, "not a chain checkpoint (too short)");
+  std::memcpy(&h, blob, sizeof h);
+  if (std::memcmp(h.magic, CHAIN_MAGIC, 8) != 0 || h.version != 1)
+    return fail(ctx, BPS_EINVAL, "not a chain checkpoint of this library version");
+  if (h.N != ctx->N || h.n_sub != ctx->nsub[0] || h.n_bins != ctx->cfg.n_bins || h.box != ctx->box[0])
+    return fail(ctx, BPS_EINVAL, "checkpoint of another grid, box, subsample or bin count");
+  if (bytes != chain_blob_bytes(ctx)) return fail(ctx, BPS_EINVAL, "checkpoint size does not match the grid");
+  if (h.n_mass < 0 || h.n_mass > MAXB || !(h.eps_max > 0.0) || !std::isfinite(h.eps_max))
+    return fail(ctx, BPS_EINVAL, "corrupt checkpoint header");
+  for (int m = 0; m < h.n_bins; ++m)
+    if (!(h.P[m] > 0.0) || !std::isfinite(h.P[m]) || !(h.P_ref[m] > 0.0) || !std::isfinite(h.P_ref[m]))
+      return fail(ctx, BPS_EINVAL, "corrupt checkpoint spectrum");
+  bps_status st = BPS_OK;
+  if (h.n_mass > 0) {
+    double sc[MAXB];
+    std::memcpy(sc, h.mass_scale, sizeof sc);
+    st = bps_set_mass_scale(ctx, h.n_mass, sc);
+    if (st != BPS_OK) return st;
+  }
+  st = ds_write_bytes(ctx, 0, DS_OFF(P), h.P, sizeof(h.P));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, 0, DS_OFF(P_ref), h.P_ref, sizeof(h.P_ref));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, 0, DS_OFF(b), h.b, sizeof(h.b));
+  if (st == BPS_OK) st = ds_write_bytes(ctx, 0, DS_OFF(nbar), h.nbar, sizeof(h.nbar));
+  unsigned long long it = h.iteration;
+  if (st == BPS_OK) st = ds_write_bytes(ctx, 0, DS_OFF(iteration), &it, sizeof(it));
+  if (st != BPS_OK) return st;
+  if (h.eps_max != ctx->cfg.eps_max) {
+    ctx->cfg.eps_max = h.eps_max;
+    drop_graph(ctx);   // eps_max is a launch argument of the captured iteration
+  }
+  int cur = current_buffer(ctx, 0, &st);
+  if (st != BPS_OK) return st;
+  const size_t H1 = (size_t)ctx->N / 2 + 1;
+  CK(cudaMemcpy2DAsync(ctx->dh[cur], (size_t)ctx->zp * sizeof(float2), static_cast<const char*>(blob) + sizeof h,
+                       H1 * sizeof(float2), H1 * sizeof(float2), (size_t)ctx->N * ctx->N, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  if (ctx->have_data[0]) {
+    st = rebuild_chain(ctx, 0);
+    if (st != BPS_OK) return st;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BPS_OK;
+}
+
+bps_status bps_selftest_wait(bps_ctx* ctx, uint64_t limit_ns) {
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "null argument or batch context");
+  if (limit_ns < 1 || limit_ns > 1000000000ULL) return fail(ctx, BPS_EINVAL, "limit_ns must be in 1..1e9");
+  bps_status st = check_status(ctx);   // report (and clear) anything earlier first
+  if (st != BPS_OK) return st;
+  launch_wait_probe(ctx->ds, (unsigned long long)limit_ns, ctx->stream);
+  LAUNCHED(ctx, 1);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
 }
 
 bps_status bps_hmc_step(bps_ctx* ctx, bps_move_info* info) {

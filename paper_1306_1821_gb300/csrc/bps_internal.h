@@ -17,6 +17,8 @@ struct PassTable {
   int N, zp, F, x_tiles, z_tiles;
   void (*x_init)(const Fields&, int region, int nch, cudaStream_t);
   void (*x_leap)(const Fields&, int first, int nch, cudaStream_t);
+  // the first leapfrog step, also reducing sum w |g|^2 / M of the start force into `region`
+  void (*x_leapg)(const Fields&, int region, int nch, cudaStream_t);
   void (*x_final)(const Fields&, int region, int nch, cudaStream_t);
   void (*x_inv)(const Fields&, int src_buf, float2* dst, int nch, cudaStream_t);   // src_buf -1: current state; dst NULL: W
   void (*x_fwd)(const Fields&, int src_buf, float2* dst, int nch, cudaStream_t);   // dst NULL: current state
@@ -104,6 +106,10 @@ void launch_zero_dc(float2* spec, cudaStream_t s);
 
 enum JumpKind { J_FIRST = 0, J_MID = 1, J_LAST = 2 };
 
+// bounded-wait self-test: a wait that no copy completes, limited to limit_ns;
+// sets ST_TIMEOUT in ds->status (bps_draws.cu)
+void launch_wait_probe(DevState* ds, unsigned long long limit_ns, cudaStream_t s);
+
 // Device copy of the mass-preconditioner network for inference inside the
 // Gibbs iteration (bps_mlp.cu).  Before a move, launch_mass_net writes
 // DevState::mass_scale[j] = exp(clamp(net(z)_j)) per chain, with z the
@@ -113,6 +119,15 @@ bps_status massnet_create(const bps_mlp* net, const float* mean, const float* sd
 void massnet_destroy(MassNet* m);
 int massnet_width(const bps_mlp* net, int output);   // input width (output = 0) or output width (1)
 void launch_mass_net(const ScalarArgs& a, const MassNet* m, int nch, cudaStream_t s);
+
+// Power-spectrum bins (bps_api.cu), the one definition every entry point uses:
+// n_bins linear bins in |n| over (0, sqrt(3) N / 2], binned on the integer |n|^2.
+int bin_of_host(long long n2, int N, int nb);
+// thresholds thr[m] = smallest |n|^2 of bin m (and full-grid mode counts when
+// nmodes is not NULL); false when a bin has no threshold or, with nmodes, no mode
+bool bin_tables(int N, int nb, int* thr, double* nmodes);
+// every bin holds at least one wave vector of the grid (N <= 512; no allocation)
+bool bins_have_modes(int N, int nb, const int* thr);
 
 // Text returned by bps_last_error(NULL) for context-free calls.
 void set_last_error(const char* msg);

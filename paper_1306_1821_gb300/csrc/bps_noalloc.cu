@@ -6,6 +6,8 @@
 // of fixed size instead of a buffer from cudaMalloc.  See bps_bin_power_noalloc
 // in include/bps.h for the contract.
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 #include "bps_internal.h"
@@ -83,23 +85,6 @@ __global__ void __launch_bounds__(256) k_na_finish(const double* part, double sc
 std::mutex g_na_mu;
 double* g_na_ptr[64] = {nullptr};
 
-// bin thresholds (smallest |n|^2 of each bin) of n_bins linear bins over
-// (0, sqrt(3) N / 2]; false when a bin receives no integer |n|^2
-bool na_thresholds(int N, int nb, int* thr) {
-  for (int m = 0; m < MAXB; ++m) thr[m] = 0x7fffffff;
-  thr[0] = 0;
-  const long long maxn2 = 3LL * (N / 2) * (N / 2);
-  int prev = 0;
-  for (long long n2 = 1; n2 <= maxn2; ++n2) {
-    double b = std::floor((double)nb * std::sqrt((double)n2) / (std::sqrt(3.0) * (double)N / 2.0));
-    int m = (int)b > nb - 1 ? nb - 1 : (int)b;
-    while (prev < m) thr[++prev] = (int)n2;
-  }
-  for (int m = 1; m < nb; ++m)
-    if (thr[m] == 0x7fffffff) return false;
-  return true;
-}
-
 }  // namespace
 }  // namespace bps
 
@@ -123,9 +108,15 @@ extern "C" bps_status bps_bin_power_noalloc(int grid_n, double box_len, int n_bi
     set_last_error("box length must be positive");
     return BPS_EINVAL;
   }
+  if ((reinterpret_cast<uintptr_t>(spec_dev) & 7) || (reinterpret_cast<uintptr_t>(sigma_dev) & 7)) {
+    set_last_error("spec_dev and sigma_dev must be 8-byte aligned (complex64 and double arrays)");
+    return BPS_EINVAL;
+  }
+  // the bins of bps_create, with the same validation: every bin needs a
+  // threshold and at least one wave vector of the grid
   Thr thr;
-  if (!na_thresholds(grid_n, n_bins, thr.t)) {
-    set_last_error("a bin receives no |n|^2 value; use fewer bins");
+  if (!bin_tables(grid_n, n_bins, thr.t, nullptr) || !bins_have_modes(grid_n, n_bins, thr.t)) {
+    set_last_error("a bin holds no mode of the grid; use fewer bins");
     return BPS_EINVAL;
   }
   int dev = 0;
@@ -148,6 +139,16 @@ extern "C" bps_status bps_bin_power_noalloc(int grid_n, double box_len, int n_bi
       g_na_ptr[dev] = static_cast<double*>(p);
     }
     part = g_na_ptr[dev];
+  }
+  // an error left by earlier, unrelated work is reported as such and left in
+  // place, not taken for a failure of these launches
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "a CUDA error was already pending before this call: %s",
+                  cudaGetErrorName(pending));
+    set_last_error(msg);
+    return BPS_ECUDA;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const double vc = std::pow(box_len / grid_n, 3);

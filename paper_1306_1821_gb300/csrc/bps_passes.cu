@@ -28,7 +28,8 @@ enum XMode {
   X_BINPOW,     // per-bin sum w |delta|^2
   X_MACC,       // acc += delta; per mass-bin sum w |delta|^2
   X_MMEAN,      // per mass-bin sum w |acc|^2
-  X_WPOW        // per-bin sum w |W|^2 (the power of whatever W holds)
+  X_WPOW,       // per-bin sum w |W|^2 (the power of whatever W holds)
+  X_LEAPG       // X_LEAP of the first step, also reducing g^T M^-1 g of the force it applies
 };
 
 enum ZMode { Z_GRAD = 0, Z_NOISE, Z_R2C, Z_C2R, Z_SUMS };
@@ -95,7 +96,7 @@ __device__ __forceinline__ const float2* buf_ptr(const Fields& fp, int b) {
 
 // ------------------------------------------------------------------ x pass
 template <int N, int MODE>
-__global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_BLOCKS
+__global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG ? BPS_XLEAP_MIN_BLOCKS
                                               : MODE == X_JINV  ? BPS_XJINV_MIN_BLOCKS
                                               : MODE == X_JGRAD ? BPS_XJGRAD_MIN_BLOCKS
                                                                 : BPS_XPASS_MIN_BLOCKS)
@@ -169,8 +170,8 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
   };
 
   // ---------------- modes that start from a spatial-x tile: forward transform
-  if constexpr (MODE == X_INIT || MODE == X_LEAP || MODE == X_FINAL || MODE == X_FWD || MODE == X_GRAD ||
-                MODE == X_JGRAD) {
+  if constexpr (MODE == X_INIT || MODE == X_LEAP || MODE == X_LEAPG || MODE == X_FINAL || MODE == X_FWD ||
+                MODE == X_GRAD || MODE == X_JGRAD) {
     const float2* in = (MODE == X_INIT) ? fp.ph : (MODE == X_FWD) ? buf_ptr(fp, xa.src_buf) : fp.W;
     // X_FWD with no destination writes the current state buffer
     if (ja < R1) {
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
 
   if constexpr (MODE == X_INIT) {
     // momentum p = sqrt(M_k) FFT(xi); kinetic energy (1/2N^3) sum w |p|^2 / M
-    float eK = 0.f, eP = 0.f;
+    TwoSumAcc eK, eP;
     float2 x[R1];
     if (act) {
 #pragma unroll
@@ -205,9 +206,9 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
         const int m = mode_bin(k, il, im, sm);
         float2 p = m >= 0 ? cscale(v[d], sm) : make_float2(0.f, 0.f);
         fp.ph[colo + (long long)k * T.rs] = p;
-        eK += wk * (p.x * p.x + p.y * p.y) * im;
+        eK.add(wk * (p.x * p.x + p.y * p.y) * im);
         float2 xx = m >= 0 ? x[d] : make_float2(0.f, 0.f);
-        eP += wk * (xx.x * xx.x + xx.y * xx.y) * il;
+        eP.add(wk * (xx.x * xx.x + xx.y * xx.y) * il);
         v[d] = xx;
       }
     }
@@ -216,8 +217,8 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
 #pragma unroll
       for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
     }
-    double sK = block_sum<NT>((double)eK, s_red);
-    double sP = block_sum<NT>((double)eP, s_red);
+    double sK = block_sum<NT>(eK.value(), s_red);
+    double sP = block_sum<NT>(eP.value(), s_red);
     if (t == 0) {
       fp.part[xa.region + blockIdx.x] = sK;
       fp.part[xa.region + fp.part_stride + blockIdx.x] = sP;
@@ -225,11 +226,13 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
     return;
   }
 
-  if constexpr (MODE == X_LEAP) {
-    const float2* src = xa.first ? dsel(fp, cur) : dsel(fp, 1 - cur);
+  if constexpr (MODE == X_LEAP || MODE == X_LEAPG) {
+    const bool first = MODE == X_LEAPG || xa.first;
+    const float2* src = first ? dsel(fp, cur) : dsel(fp, 1 - cur);
     float2* dst = dsel(fp, 1 - cur);
     const float eps = (float)ds->eps;
-    const float ek = xa.first ? 0.5f * eps : eps;
+    const float ek = first ? 0.5f * eps : eps;
+    float eG = 0.f;   // X_LEAPG: sum w |g|^2 / M of the force at the start point
     // the column in parts: the loads of a part in flight together, at a
     // fraction of the registers of a whole column
     constexpr int HALF = R1 / BPS_XLEAP_CHUNKS > 0 ? R1 / BPS_XLEAP_CHUNKS : 1;
@@ -252,6 +255,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
         float2 xx = x[q], pp = p[q];
         if (m >= 0) {
           const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
+          if constexpr (MODE == X_LEAPG) eG += wk * (gx * gx + gy * gy) * im;
           pp.x = fmaf(-ek, gx, pp.x);
           pp.y = fmaf(-ek, gy, pp.y);
           const float s = eps * im;
@@ -273,6 +277,10 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
 #pragma unroll
       for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
     }
+    if constexpr (MODE == X_LEAPG) {
+      const double sG = block_sum<NT>((double)eG, s_red);
+      if (t == 0) fp.part[xa.region + blockIdx.x] = sG;
+    }
     return;
   }
 
@@ -280,7 +288,8 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
     const float2* src = dsel(fp, 1 - cur);
     const float eps = (float)ds->eps;
     const float ek = 0.5f * eps;
-    float eK = 0.f, eP = 0.f;
+    TwoSumAcc eK, eP;
+    float eG = 0.f;   // sum w |g|^2 / M of the last force (the Delta H identity of k_move_end)
     float2 x[R1], p[R1];
     if (act) {
 #pragma unroll
@@ -297,24 +306,27 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
         if (m >= 0) {
           float2 xx = x[d], pp = p[d];
           const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
+          eG += wk * (gx * gx + gy * gy) * im;
           pp.x = fmaf(-ek, gx, pp.x);
           pp.y = fmaf(-ek, gy, pp.y);
-          eK += wk * (pp.x * pp.x + pp.y * pp.y) * im;
-          eP += wk * (xx.x * xx.x + xx.y * xx.y) * il;
+          eK.add(wk * (pp.x * pp.x + pp.y * pp.y) * im);
+          eP.add(wk * (xx.x * xx.x + xx.y * xx.y) * il);
         }
       }
     }
-    double sK = block_sum<NT>((double)eK, s_red);
-    double sP = block_sum<NT>((double)eP, s_red);
+    double sK = block_sum<NT>(eK.value(), s_red);
+    double sP = block_sum<NT>(eP.value(), s_red);
+    double sG = block_sum<NT>((double)eG, s_red);
     if (t == 0) {
       fp.part[xa.region + blockIdx.x] = sK;
       fp.part[xa.region + fp.part_stride + blockIdx.x] = sP;
+      fp.part[xa.region + 2 * fp.part_stride + blockIdx.x] = sG;
     }
     return;
   }
 
   if constexpr (MODE == X_GRAD) {
-    float eP = 0.f;
+    TwoSumAcc eP;
     if (act) {
       float2 x[R1];
 #pragma unroll
@@ -327,12 +339,12 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP    ? BPS_XLEAP_MIN_
         float2 g = make_float2(0.f, 0.f);
         if (m >= 0) {
           g = make_float2(fmaf(x[d].x, il, v[d].x), fmaf(x[d].y, il, v[d].y));
-          eP += wk * (x[d].x * x[d].x + x[d].y * x[d].y) * il;
+          eP.add(wk * (x[d].x * x[d].x + x[d].y * x[d].y) * il);
         }
         xa.dst[colo + (long long)k * T.rs] = g;
       }
     }
-    double sP = block_sum<NT>((double)eP, s_red);
+    double sP = block_sum<NT>(eP.value(), s_red);
     if (t == 0) fp.part[xa.region + blockIdx.x] = sP;
     return;
   }
@@ -760,7 +772,10 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
     // likelihood energy (1/2) sum (a delta^2 - 2 c delta).  a and c are read from
     // global memory on the support only (not staged: shared memory would cap the
     // resident tiles of this latency-bound pass).
-    float e = 0.f;
+    // the energy only where it is asked for (the last force evaluation of a
+    // trajectory): the compensated sum costs issue slots this pass is short of
+    TwoSumAcc e;
+    const bool want_e = za.region >= 0;
     if (f < LP) {
       const int loa = s_lo[2 * f], hia = s_hi[2 * f], lob = s_lo[2 * f + 1], hib = s_hi[2 * f + 1];
 #pragma unroll
@@ -772,12 +787,15 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
         const float ab = inb ? __ldg(fp.a + gb0) : 0.f, cb = inb ? __ldg(fp.c + gb0) : 0.f;
         const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
         const float ga = fmaf(aa, da, -ca), gb = fmaf(ab, db, -cb);
-        e += da * (ga - ca) + db * (gb - cb);   // a d^2 - 2 c d
+        if (want_e) {                           // a d^2 - 2 c d
+          e.add(da * (ga - ca));
+          e.add(db * (gb - cb));
+        }
         v[d] = make_float2(ga, gb);
       }
     }
-    if (za.region >= 0) {
-      double s = block_sum<NTZ>(0.5 * (double)e, s_red);
+    if (want_e) {
+      double s = block_sum<NTZ>(0.5 * e.value(), s_red);
       if (t == 0) fp.part[za.region + blockIdx.x] = s;
     }
   }
@@ -991,6 +1009,7 @@ static PassTable make_table() {
   T.z_tiles = C::ZTILES;
   T.x_init = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_INIT>(f, XArgs{-1, nullptr, 0, region}, n, s); };
   T.x_leap = [](const Fields& f, int first, int n, cudaStream_t s) { L::template x<X_LEAP>(f, XArgs{-1, nullptr, first, -1}, n, s); };
+  T.x_leapg = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_LEAPG>(f, XArgs{-1, nullptr, 1, region}, n, s); };
   T.x_final = [](const Fields& f, int region, int n, cudaStream_t s) { L::template x<X_FINAL>(f, XArgs{-1, nullptr, 0, region}, n, s); };
   T.x_inv = [](const Fields& f, int src, float2* dst, int n, cudaStream_t s) { L::template x<X_INV>(f, XArgs{src, dst, 0, -1}, n, s); };
   T.x_fwd = [](const Fields& f, int src, float2* dst, int n, cudaStream_t s) { L::template x<X_FWD>(f, XArgs{src, dst, 0, -1}, n, s); };

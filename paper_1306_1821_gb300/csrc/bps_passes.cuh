@@ -196,6 +196,24 @@ __device__ __forceinline__ int bin_est(int n2, const int* thr, float scale, int 
 }
 
 // ------------------------------------------------------------ reductions
+// Per-thread FP32 running sum that keeps the rounding error of every addition
+// (Knuth's TwoSum, error-free for round-to-nearest: s + c carries the exact sum
+// of the terms up to the last compensation add).  The Hamiltonian terms of a
+// 256^3 grid are summed over 10^7 modes; with plain FP32 partials of 16-32
+// terms each partial rounds at ~1e-7 of itself and the sum over all partials
+// loses ~1e-3 in absolute energy, the size of the Delta H tolerance.  The
+// intrinsics keep the compiler from contracting or reordering the steps.
+struct TwoSumAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

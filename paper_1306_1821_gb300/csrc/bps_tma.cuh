@@ -36,8 +36,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Wait for phase `parity` of the barrier; false after WAIT_LIMIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of the barrier; false after limit_ns (WAIT_LIMIT_NS
+// unless a caller asks for less).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
   const uint32_t a = smem_u32(bar);
   uint32_t done = 0;
   unsigned long long t0 = 0;
@@ -51,7 +53,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     if (done) return true;
     if (it == 0) t0 = global_ns();
-    else if ((it & 63) == 0 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    else if ((it & 63) == 0 && global_ns() - t0 > limit_ns) return false;
   }
 }
 

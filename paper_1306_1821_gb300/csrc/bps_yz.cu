@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(YZ<N, CL>::NT, 2) k_yzpass(Fields fp0, int reg
       }
     }
     fft2<N, R2, R1, INV, MAP_ROW, LP>(v, ex, twN, t);
-    float e = 0.f;
+    TwoSumAcc e;   // compensated: see TwoSumAcc
     {
       const int f = t / R1, c = t % R1;
       if (f < LP) {
@@ -242,12 +242,15 @@ __global__ void __launch_bounds__(YZ<N, CL>::NT, 2) k_yzpass(Fields fp0, int reg
           const float ab = inb ? pa[lb + n] : 0.f, cb = inb ? pc[lb + n] : 0.f;
           const float da = v[d].x * fp.inv_nv, db = v[d].y * fp.inv_nv;
           const float ga = fmaf(aa, da, -ca), gb = fmaf(ab, db, -cb);
-          e += da * (ga - ca) + db * (gb - cb);          // a d^2 - 2 c d
+          if (region >= 0) {                             // a d^2 - 2 c d
+            e.add(da * (ga - ca));
+            e.add(db * (gb - cb));
+          }
           v[d] = make_float2(ga, gb);
         }
       }
     }
-    eacc += (double)e;
+    eacc += e.value();
     fft2<N, R1, R2, FWD, MAP_ROW, LP>(v, ex, twN, t);
     {
       const int f = t / R2, c = t % R2;

@@ -72,3 +72,40 @@ def gpu_spectrum(s):
     out = torch.zeros((N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
     bps.bps_get_spectrum(s.ctx, out)
     return out.cpu().numpy().astype(np.complex128)
+
+
+def compare_chain(rec, ch, n_iter, tol_dH=1e-3, tol_P=1e-4, tol_b=1e-3, tol_nbar=1e-4, on_iteration=None):
+    """Compare GPU chain records rec [n_iter][n_bins + 2 n_sub + 2] with the oracle
+    chain `ch` (advanced here), iteration by iteration.
+
+    The two sides take the same Philox draws, so they take the same Metropolis
+    decisions unless |dH + ln u| falls inside the FP32 band tol_dH (HMC move and
+    jump, Eq. acceptance_rule); after such an iteration the chains are both
+    valid but no longer comparable, and the comparison stops.  Returns the
+    number of iterations compared and the largest |dH_gpu - dH_oracle|."""
+    import math
+
+    from oracle import hmc, philox
+    nb, ns = len(ch.P), len(ch.b)
+    worst = 0.0
+    for i in range(n_iter):
+        it = ch.iteration
+        r = ch.iterate()
+        got = rec[i]
+        h = r["hmc"]
+        err = abs(got[-2] - h["dH"])
+        worst = max(worst, err)
+        assert err < tol_dH, (i, got[-2], h["dH"])
+        near = abs(h["dH"] + math.log(h["u_acc"])) < tol_dH
+        if "jump" in r:
+            u_j = hmc.move_uniforms(ch.seed, it, stage=philox.STAGE_JUMP)[1]
+            near = near or abs(r["jump"]["dH"] + math.log(u_j)) < tol_dH
+        if near:
+            return i, worst
+        assert int(got[-1]) == int(h["accepted"]), i
+        assert np.max(np.abs(got[:nb] / r["P"] - 1)) < tol_P, (i, got[:nb], r["P"])
+        assert np.max(np.abs(got[nb:nb + ns] - r["b"])) < tol_b, (i, got[nb:nb + ns], r["b"])
+        assert np.max(np.abs(got[nb + ns:nb + 2 * ns] / r["nbar"] - 1)) < tol_nbar, (i,)
+        if on_iteration is not None:
+            on_iteration(i, r)
+    return n_iter, worst

@@ -138,3 +138,43 @@ def test_batch_with_network_mass_equals_single_contexts():
     finally:
         bps.bps_destroy(batch)
         net.close()
+
+
+def test_batch_of_the_96_chain_workload_sizes_matches_oracles():
+    """Chains drawn from the 96-chain batch workload (32^3, 64^3 and 96^3 grids,
+    caps of 20-60% of the sky with linear fall-off, 3-4 subsamples, 16 bins,
+    jump on): two Gibbs iterations of each against its own oracle chain, the
+    96^3 chains taking the radix-3 transform path inside the batch."""
+    import torch
+
+    from paper_1306_1821_gb300 import bps
+    from tests.helpers import compare_chain
+    wls = inputs.batch_workloads()
+    pick = [wls[j] for j in (3, 32, 34, 66, 67)]
+    cfg = bps.make_config(16, n_leapfrog=10, eps_max=0.1, jump=1, jump_leapfrog=4, jump_eps_max=0.2,
+                          fixed_bias_index=0, seed=500)
+    batch = bps.bps_create_batch([w.N for w in pick], [w.box for w in pick], [w.n_sub for w in pick], cfg)
+    try:
+        starts = []
+        for j, wl in enumerate(pick):
+            delta, counts, R = inputs.make_survey(wl)
+            d32 = (0.8 * delta).astype(np.float32)
+            P, b, nbar = inputs.initial_state(wl)
+            bps.bps_batch_set_chain(batch, j, torch.from_numpy(counts).cuda(), torch.from_numpy(R).cuda(),
+                                    torch.from_numpy(d32).cuda(), P, b, nbar, 0)
+            starts.append((counts, R, d32, P, b, nbar))
+        n_iter = 2
+        rec = bps.bps_batch_gibbs_iterate(batch, n_iter, len(pick))
+        for j, wl in enumerate(pick):
+            counts, R, d32, P, b, nbar = starts[j]
+            g = grid.Geometry(wl.N, wl.box, 16)
+            dh = grid.forward(d32.astype(np.float64))
+            dh[0, 0, 0] = 0
+            ch = gibbs.Chain(g, counts, R, P, b, nbar, delta_hat=dh, n_leapfrog=10, eps_max=0.1, jump=True,
+                             jump_leapfrog=4, jump_eps_max=0.2, fixed_bias=0, seed=500 + j)
+            slot = bps.bps_batch_record_slot(batch, j)
+            L = 16 + 2 * wl.n_sub + 2
+            done, worst = compare_chain(rec[:, slot, :L], ch, n_iter)
+            assert done >= 1, (j, wl.N)
+    finally:
+        bps.bps_destroy(batch)

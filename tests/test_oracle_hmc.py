@@ -181,3 +181,34 @@ def test_mass_multipliers_leave_the_closed_form_conditional_unchanged():
     for lev in levels[levels > 0]:
         sel = (g.n2 == lev)[obs]
         assert abs(r[sel].mean() - 1.0) < 0.15, (lev, r[sel].mean())
+
+
+def test_leapfrog_energy_error_telescopes_for_quadratic_potential():
+    # The potential of the density move is exactly quadratic in delta (Eq.
+    # Wiener_Posterior_psi at fixed P, b, Nbar), and for kick-drift-kick
+    # leapfrog on a quadratic potential each step changes H by
+    # (eps^2/8)(g_{n+1}^T M^-1 g_{n+1} - g_n^T M^-1 g_n), so the energy error of
+    # a whole trajectory is (eps^2/8)(g_L^T M^-1 g_L - g_0^T M^-1 g_0).  The CUDA
+    # library evaluates Delta H of Eq. acceptance_rule this way; here the
+    # identity is checked against the direct difference H1 - H0 of the oracle,
+    # with and without mass multipliers.
+    g, P, a, c, *_ = setup(N=16, n_sub=2, n_bins=4, seed=3)
+    d0 = inputs.random_spectrum(g.N, g.n_bins, 1, 0.3)
+    d0[0, 0, 0] = 0
+
+    def gnorm(d, invM):
+        gh, _ = model.gradient_hat(g, d, P, a, c)
+        return np.sum(g.w * np.abs(gh) ** 2 * invM) / g.Nv
+
+    levels = np.unique(g.n2)
+    per_level = dict(zip(levels.tolist(), np.exp(np.random.default_rng(2).uniform(-1, 1, len(levels)))))
+    for scale in (None, np.vectorize(per_level.get)(g.n2).astype(np.float64)):
+        M, invM = model.mass_diag(g, P, a.mean(), scale)
+        p0 = hmc.draw_momentum(g, M, 5, 0)
+        H0 = model.hamiltonian(g, d0, p0, P, a, c, invM)
+        for eps, L in [(0.05, 3), (0.1, 7), (0.3, 20)]:
+            d1, p1, _ = hmc.leapfrog(g, d0, p0, eps, L, P, a, c, invM)
+            dH = model.hamiltonian(g, d1, p1, P, a, c, invM) - H0
+            ident = eps ** 2 / 8.0 * (gnorm(d1, invM) - gnorm(d0, invM))
+            assert abs(dH) > 1e-2
+            assert abs(dH - ident) < 1e-10 * max(1.0, abs(dH))
