@@ -16,6 +16,8 @@ Modules (each function cites the section or equation it follows):
     draws   Gamma (Marsaglia-Tsang), GIG (ratio of uniforms), normals
     gibbs   P / b / Nbar conditionals, the P-delta jump, the Gibbs scan
     mlp     the mass-preconditioner network (forward, backward, Adam)
+    mock    artificial surveys of Sec. 5: field, Poisson and Gaussian counts,
+            Schechter selection and mean numbers, bias law, survey response
 
 Pins: every function is checked in tests/test_oracle_*.py against something
 other than itself (closed forms, dense linear algebra, finite differences,
@@ -23,4 +25,4 @@ quadrature, scipy distributions, an independent Philox implementation).
 Parity unpinned: only the sampler's efficiency figures (acceptance ~92%,
 correlation length, burn-in length), which the paper reports for its own data.
 """
-from . import draws, gibbs, grid, hmc, mlp, model, philox  # noqa: F401
+from . import draws, gibbs, grid, hmc, mlp, mock, model, philox  # noqa: F401
