@@ -382,6 +382,80 @@ bps_status bps_voxel_normals(uint64_t seed, uint64_t iteration, size_t n, float*
 bps_status bps_bin_power_noalloc(int grid_n, double box_len, int n_bins, const float* spec_dev,
                                  double* sigma_dev, void* cuda_stream);
 
+/* ---- artificial surveys (Sec. 5; App. D; Eq. rel_bias) ----
+ * Generated on the device, for fast sweeps over survey configurations; the
+ * random numbers come from Philox4x64-10 with key `seed`, stage 8 for the field
+ * and stage 9 for the counts, so any implementation of the same definitions
+ * reproduces them.  Each call works on the single-chain context's grid (N, box,
+ * n_sub of bps_create), queues on its stream and does not synchronise; the
+ * context keeps one small device table for them until bps_destroy. */
+
+/* True density field (Sec. 5): delta = IFFT(A_k FFT(xi)), A_k = sqrt(P_k /
+ * V_cell) (forward transform unnormalised, inverse 1/N^3, so E|delta_k|^2 =
+ * N^3 P_k / V_cell as in the prior of Eq. dens_prior), with xi the FP32 normals
+ * of stream (seed, 0, 8, 0) laid out as in bps_voxel_normals.  P_n2 (host,
+ * 3 (N/2)^2 + 1 doubles) is the power at every integer |n|^2 (P_n2[0] is
+ * ignored: the k = 0 mode is zero); delta_dev float32 [N][N][N] (device).
+ * BPS_EINVAL for a negative or non-finite P. */
+bps_status bps_mock_field(bps_ctx* ctx, uint64_t seed, const double* P_n2, float* delta_dev);
+
+/* Galaxy counts of every subsample l (Eq. data_model) from the true field
+ * delta_dev and the response R_dev (float32 [n_sub][N][N][N], device), with
+ * b[l], nbar[l] (host):
+ *   noise 0: N ~ Poisson(lambda), lambda = (R Nbar) max(0, 1 + b delta), drawn by
+ *     inversion of the Poisson distribution function in chunks of mean <= 32
+ *     (their sum is Poisson with the summed mean), in FP64 operations that IEEE
+ *     754 rounds exactly (e^-mu by halving, a degree-10 Taylor series and ten
+ *     squarings); chunk j of voxel i reads word j % 4 of block
+ *     (i, j / 4, 9, l).  A mean above 4096 gives the count 65536, which
+ *     bps_set_data rejects.
+ *   noise 1: the paper's Gaussian noise (Sec. 5, Eq. cov_mat_noise),
+ *     N = Nbar R (1 + b delta) + sqrt(Nbar R) z, z the FP64 Box-Muller normal of
+ *     words 0, 1 of block (i, 0, 9, l), rounded to the nearest integer (halves
+ *     up) and clipped at 0, since counts are stored as integers.
+ * counts_dev int32 [n_sub][N][N][N] (device). */
+bps_status bps_mock_counts(bps_ctx* ctx, uint64_t seed, const float* delta_dev, const float* R_dev, const double* b,
+                           const double* nbar, int noise, int32_t* counts_dev);
+
+/* Survey response R^l_i = C_i f^l(r_i) (Sec. 5, the equation for R^l_i): the
+ * completeness C is a spherical cap of sky fraction f_sky about axis[3]
+ * (host; cos(theta) >= 1 - 2 f_sky, the SDSS mask itself is not available)
+ * inside r <= box/2 about the box centre (the observer); f^l is the table
+ * (host, [n_sub][n_r] doubles) of the radial selection at r_j = j (box/2) /
+ * (n_r - 1), interpolated linearly.  All geometry in FP64 without fused
+ * operations, so the zero pattern is exact.  R_dev float32 [n_sub][N][N][N]. */
+bps_status bps_mock_response(bps_ctx* ctx, double f_sky, const double* axis, int n_r, const double* table,
+                             float* R_dev);
+
+/* Schechter luminosity function (App. D) and the apparent-magnitude limits of
+ * a flux-limited survey (Sec. 5): Phi(M) dM = 0.4 ln10 Phi_* x^(alpha+1) e^-x dM,
+ * x = 10^(0.4 (M_star - M)), magnitudes M - 5 log10 h. */
+typedef struct {
+  double M_star;    /* -20.44 in the paper */
+  double alpha;     /* -1.05 */
+  double m_bright;  /* 14.5 */
+  double m_faint;   /* 17.77 */
+  double omega_m;   /* flat LCDM for the luminosity distance (0.24) */
+} bps_schechter;
+
+/* Radial selection tables and mean numbers of n_sub absolute-magnitude bins
+ * [M_edges[l], M_edges[l+1]] (host, increasing: brightest first), host code:
+ *   table[l][j] = int_{M_lo(r_j)}^{M_hi(r_j)} Phi dM / int_{M_edges[l]}^{M_edges[l+1]} Phi dM
+ * with r_j = j r_max / (n_r - 1) comoving (Mpc/h) and [M_lo, M_hi] the part of
+ * the bin whose apparent magnitude m = M + 5 log10(D_L) + 25 lies within
+ * [m_bright, m_faint], D_L = (1 + z) r (flat LCDM, no K-correction); and
+ * nbar_rel[l] = int over the bin of Phi with Phi_* = 1 (Sec. 5: Nbar^l is this
+ * integral times Phi_*; may be NULL).  Integrals by composite 16-point
+ * Gauss-Legendre quadrature. */
+bps_status bps_schechter_tables(const bps_schechter* s, int n_sub, const double* M_edges, double r_max, int n_r,
+                                double* table, double* nbar_rel);
+
+/* Luminosity-dependent bias, Eq. rel_bias: b_out[l] = b_star (a + b 10^(0.4
+ * (M_star - M[l])) + c (M[l] - M_star)) (host arrays; the paper uses a = 0.895,
+ * b = 0.105, c = -0.040, M_star = -20.83, b_star = 1.2). */
+bps_status bps_bias_law(int n, const double* M, double b_star, double M_star, double a, double b, double c,
+                        double* b_out);
+
 /* Library version string and the text of the last error of ctx (or of the
  * last failed context-free call when ctx is NULL). */
 const char* bps_version(void);

@@ -93,8 +93,9 @@ def exp_neg(mu):
     return s
 
 
-def poisson_counts(lam, seed, sub):
-    """Poisson variates of the flattened means `lam` (voxel index = position)."""
+def poisson_counts(lam, seed, sub, index=None):
+    """Poisson variates of the flattened means `lam`; `index` gives each entry's
+    voxel index (its Philox counter), by default its position."""
     lam = np.asarray(lam, dtype=np.float64).ravel()
     if np.any(lam > LAMBDA_MAX) or np.any(lam < 0):
         raise ValueError("means must lie in [0, 4096]")
@@ -103,7 +104,7 @@ def poisson_counts(lam, seed, sub):
     mu = np.where(K > 0, lam / np.maximum(K, 1.0), 0.0)
     e = exp_neg(mu)
     out = np.zeros(n, dtype=np.int64)
-    vox = np.arange(n, dtype=np.uint64)
+    vox = np.arange(n, dtype=np.uint64) if index is None else np.asarray(index, dtype=np.uint64).ravel()
     kmax = int(K.max()) if n else 0
     for j in range(kmax):
         act = K > j
@@ -137,11 +138,13 @@ def mean_counts(delta, R, b, nbar, linear=False):
     return (np.asarray(R, dtype=np.float64) * nbar) * t
 
 
-def gaussian_counts(delta, R, b, nbar, seed, sub):
-    """Counts under the paper's Gaussian noise model (rounded, clipped at 0)."""
+def gaussian_counts(delta, R, b, nbar, seed, sub, index=None):
+    """Counts under the paper's Gaussian noise model (rounded, clipped at 0);
+    `index` as for poisson_counts."""
     m = mean_counts(delta, R, b, nbar, linear=True).ravel()
     var = np.asarray(R, dtype=np.float64).ravel() * nbar
-    w = philox.words(seed, 0, STAGE_MOCK_COUNTS, sub, np.arange(m.size, dtype=np.uint64))
+    vox = np.arange(m.size, dtype=np.uint64) if index is None else np.asarray(index, dtype=np.uint64).ravel()
+    w = philox.words(seed, 0, STAGE_MOCK_COUNTS, sub, vox)
     z = philox.normal64(w[0], w[1])
     x = m + np.sqrt(var) * z
     c = np.floor(x + 0.5)

@@ -30,6 +30,16 @@ class bps_config(ctypes.Structure):
                 ("mass_mode", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
+class bps_schechter(ctypes.Structure):
+    _fields_ = [("M_star", ctypes.c_double), ("alpha", ctypes.c_double), ("m_bright", ctypes.c_double),
+                ("m_faint", ctypes.c_double), ("omega_m", ctypes.c_double)]
+
+
+# the paper's Schechter and survey parameters (Sec. 5)
+SCHECHTER_SDSS = dict(M_star=-20.44, alpha=-1.05, m_bright=14.5, m_faint=17.77, omega_m=0.24)
+BIAS_LAW_PAPER = dict(b_star=1.2, M_star=-20.83, a=0.895, b=0.105, c=-0.040)
+
+
 class bps_move_info(ctypes.Structure):
     _fields_ = [("accepted", ctypes.c_int), ("dH", ctypes.c_double), ("eps", ctypes.c_double)]
 
@@ -94,6 +104,13 @@ _SIGS = {
     "bps_save_chain": ([_P, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "bps_load_chain": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
     "bps_selftest_wait": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "bps_mock_field": ([_P, ctypes.c_uint64, _D, _P], ctypes.c_int),
+    "bps_mock_counts": ([_P, ctypes.c_uint64, _P, _P, _D, _D, ctypes.c_int, _P], ctypes.c_int),
+    "bps_mock_response": ([_P, ctypes.c_double, _D, ctypes.c_int, _D, _P], ctypes.c_int),
+    "bps_schechter_tables": ([ctypes.POINTER(bps_schechter), ctypes.c_int, _D, ctypes.c_double, ctypes.c_int, _D,
+                              _D], ctypes.c_int),
+    "bps_bias_law": ([ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                      ctypes.c_double, _D], ctypes.c_int),
     "bps_destroy": ([_P], None),
 }
 
@@ -237,6 +254,47 @@ def bps_load_chain(ctx, blob):
 
 def bps_selftest_wait(ctx, limit_ns):
     _check(ctx, load().bps_selftest_wait(ctx, int(limit_ns)))
+
+
+def bps_mock_field(ctx, seed, P_n2, delta):
+    """delta (float32 CUDA tensor [N]^3) <- the true field of Sec. 5 with power P_n2 [3 (N/2)^2 + 1]."""
+    a, p = _darr(P_n2)
+    _check(ctx, load().bps_mock_field(ctx, int(seed), p, _dptr(delta)))
+
+
+def bps_mock_counts(ctx, seed, delta, R, b, nbar, noise, counts):
+    """counts (int32 CUDA tensor [n_sub][N]^3) <- counts of Eq. data_model; noise 0 Poisson, 1 Gaussian."""
+    ab, pb = _darr(b)
+    an, pn = _darr(nbar)
+    _check(ctx, load().bps_mock_counts(ctx, int(seed), _dptr(delta), _dptr(R), pb, pn, int(noise), _dptr(counts)))
+
+
+def bps_mock_response(ctx, f_sky, axis, table, R):
+    """R (float32 CUDA tensor [n_sub][N]^3) <- cap of sky fraction f_sky about axis x the radial tables."""
+    ax, pa = _darr(axis, 3)
+    t = np.ascontiguousarray(np.asarray(table, dtype=np.float64))
+    _check(ctx, load().bps_mock_response(ctx, float(f_sky), pa, int(t.shape[-1]), t.ctypes.data_as(_D), _dptr(R)))
+
+
+def bps_schechter_tables(M_edges, r_max, n_r, M_star=-20.44, alpha=-1.05, m_bright=14.5, m_faint=17.77,
+                         omega_m=0.24):
+    """(table [n_sub][n_r], nbar_rel [n_sub]) of the Schechter selection (host code of the library)."""
+    e, pe = _darr(M_edges)
+    n_sub = e.size - 1
+    sp = bps_schechter(M_star, alpha, m_bright, m_faint, omega_m)
+    table = np.zeros((n_sub, int(n_r)))
+    nb = np.zeros(n_sub)
+    _check(None, load().bps_schechter_tables(ctypes.byref(sp), n_sub, pe, float(r_max), int(n_r),
+                                             table.ctypes.data_as(_D), nb.ctypes.data_as(_D)))
+    return table, nb
+
+
+def bps_bias_law(M, b_star=1.2, M_star=-20.83, a=0.895, b=0.105, c=-0.040):
+    m, pm = _darr(M)
+    out = np.zeros(m.size)
+    _check(None, load().bps_bias_law(int(m.size), pm, float(b_star), float(M_star), float(a), float(b), float(c),
+                                     out.ctypes.data_as(_D)))
+    return out
 
 
 def bps_hmc_step(ctx, want_info=True):

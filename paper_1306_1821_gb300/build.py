@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libbps.so")
-UNITS = ["bps_passes.cu", "bps_draws.cu", "bps_api.cu", "bps_noalloc.cu", "bps_mlp.cu", "bps_yz.cu"]
+UNITS = ["bps_passes.cu", "bps_draws.cu", "bps_api.cu", "bps_noalloc.cu", "bps_mlp.cu", "bps_yz.cu",
+         "bps_mock.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -100,6 +100,9 @@ struct bps_ctx {
   size_t ev_used[4] = {0, 0, 0, 0};
   double prof_ms[4] = {0, 0, 0, 0};
   uint64_t prof_n[4] = {0, 0, 0, 0};
+  // device table of the mock calls (amplitudes, selection), grown on demand
+  void* mock_buf = nullptr;
+  size_t mock_bytes = 0;
   std::string err;
 };
 
@@ -616,6 +619,8 @@ void free_streams(bps_ctx* c) {
 }
 
 void free_all(bps_ctx* c) {
+  if (c->mock_buf) cudaFree(c->mock_buf);
+  c->mock_buf = nullptr;
   drop_graph(c);
   free_streams(c);
   for (int k = 0; k < 4; ++k)
@@ -1479,6 +1484,75 @@ bps_status bps_load_chain(bps_ctx* ctx, const void* blob, size_t bytes) {
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return BPS_OK;
+}
+
+// ---- artificial surveys (bps_mock.cu)
+namespace {
+bps_status mock_scratch(void* owner, size_t bytes, void** out) {
+  bps_ctx* ctx = static_cast<bps_ctx*>(owner);
+  if (ctx->mock_bytes < bytes) {
+    if (ctx->mock_buf) {
+      CK(cudaStreamSynchronize(ctx->stream));   // earlier mock kernels may still read it
+      cudaFree(ctx->mock_buf);
+      ctx->mock_buf = nullptr;
+      ctx->mock_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->mock_buf, bytes) != cudaSuccess) return fail(ctx, BPS_ENOMEM, "mock table buffer");
+    ctx->mock_bytes = bytes;
+  }
+  *out = ctx->mock_buf;
+  return BPS_OK;
+}
+bps_status mock_view(bps_ctx* ctx, MockView* v, Fields* f) {
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "null argument or batch context");
+  *f = fields_at(ctx, 0);
+  v->N = ctx->N;
+  v->zp = ctx->zp;
+  v->n_sub = ctx->nsub[0];
+  v->n_sm = ctx->n_sm > 0 ? ctx->n_sm : 152;
+  v->box = ctx->box[0];
+  v->stream = ctx->stream;
+  v->pt = &ctx->pt;
+  v->f = f;
+  v->launches = &ctx->launches;
+  v->owner = ctx;
+  v->scratch = mock_scratch;
+  return BPS_OK;
+}
+bps_status mock_result(bps_ctx* ctx, bps_status st) {
+  if (st != BPS_OK && ctx) ctx->err = bps_last_error(nullptr);
+  return st;
+}
+}  // namespace
+
+bps_status bps_mock_field(bps_ctx* ctx, uint64_t seed, const double* P_n2, float* delta_dev) {
+  MockView v;
+  Fields f;
+  bps_status st = mock_view(ctx, &v, &f);
+  if (st != BPS_OK) return st;
+  if (!P_n2 || !delta_dev) return fail(ctx, BPS_EINVAL, "null argument");
+  return mock_result(ctx, mock_field(v, seed, P_n2, delta_dev));
+}
+
+bps_status bps_mock_counts(bps_ctx* ctx, uint64_t seed, const float* delta_dev, const float* R_dev, const double* b,
+                           const double* nbar, int noise, int32_t* counts_dev) {
+  MockView v;
+  Fields f;
+  bps_status st = mock_view(ctx, &v, &f);
+  if (st != BPS_OK) return st;
+  if (!delta_dev || !R_dev || !b || !nbar || !counts_dev) return fail(ctx, BPS_EINVAL, "null argument");
+  if (noise != 0 && noise != 1) return fail(ctx, BPS_EINVAL, "noise must be 0 (Poisson) or 1 (Gaussian)");
+  return mock_result(ctx, mock_counts(v, seed, delta_dev, R_dev, b, nbar, noise, counts_dev));
+}
+
+bps_status bps_mock_response(bps_ctx* ctx, double f_sky, const double* axis, int n_r, const double* table,
+                             float* R_dev) {
+  MockView v;
+  Fields f;
+  bps_status st = mock_view(ctx, &v, &f);
+  if (st != BPS_OK) return st;
+  if (!axis || !table || !R_dev) return fail(ctx, BPS_EINVAL, "null argument");
+  return mock_result(ctx, mock_response(v, f_sky, axis, n_r, table, R_dev));
 }
 
 bps_status bps_selftest_wait(bps_ctx* ctx, uint64_t limit_ns) {

@@ -129,6 +129,25 @@ bool bin_tables(int N, int nb, int* thr, double* nmodes);
 // every bin holds at least one wave vector of the grid (N <= 512; no allocation)
 bool bins_have_modes(int N, int nb, const int* thr);
 
+// Artificial surveys (bps_mock.cu): what the context-bound mock calls need of
+// a single-chain context (its transforms, W as scratch, a small table buffer).
+struct MockView {
+  int N, zp, n_sub, n_sm;
+  double box;
+  cudaStream_t stream;
+  const PassTable* pt;
+  const Fields* f;
+  uint64_t* launches;
+  void* owner;
+  bps_status (*scratch)(void* owner, size_t bytes, void** out);   // device buffer of >= bytes
+  bps_status get_scratch(size_t bytes, void** out) const { return scratch(owner, bytes, out); }
+};
+bps_status mock_field(const MockView& v, uint64_t seed, const double* P_n2, float* delta_dev);
+bps_status mock_counts(const MockView& v, uint64_t seed, const float* delta_dev, const float* R_dev, const double* b,
+                       const double* nbar, int noise, int32_t* counts_dev);
+bps_status mock_response(const MockView& v, double f_sky, const double* axis, int n_r, const double* table,
+                         float* R_dev);
+
 // Text returned by bps_last_error(NULL) for context-free calls.
 void set_last_error(const char* msg);
 

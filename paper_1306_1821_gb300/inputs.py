@@ -32,7 +32,7 @@ class Workload:
     b: list
     nbar: list
     f_sky: float
-    radial: str            # "linear" or "gauss"
+    radial: str            # "linear", "gauss" or "schechter" (selection tables, made on the device)
     r0: float = 350.0
     n_leapfrog: int = 10
     eps_max: float = 0.3
@@ -66,6 +66,31 @@ WORKLOADS = {
     "survey256": Workload("survey256", 256, 1000.0, 32, SIX_B, _six_nbar(), 0.25, "gauss",
                           n_leapfrog=20, eps_max=0.05, jump=True, jump_leapfrog=10, jump_eps_max=0.15),
 }
+
+
+# The paper's own test setup (Sec. 5) at 128^3, L = 750 Mpc/h: fifteen
+# luminosity subsamples in absolute-magnitude bins of 0.4 from -23 to -17
+# (brightest first), radial selection from the Schechter function of App. D
+# with M_* - 5 log10 h = -20.44, alpha = -1.05 inside 14.5 < r < 17.77 (flat
+# LCDM, Omega_m = 0.24), mean numbers Nbar^l = Phi_* int Phi dM over each bin
+# with Phi_* = 19.6798... (the faintest bin has Nbar = 8), and biases from the
+# luminosity law of Eq. rel_bias (b_* = 1.2, M_* = -20.83, a = 0.895,
+# b = 0.105, c = -0.040) at the bin centres.  The values below are those
+# definitions evaluated once in FP64; the DR7 mask is replaced by a 25% cap.
+SCHECHTER15_EDGES = [-23.0 + 0.4 * i for i in range(16)]
+SCHECHTER15_PHI_STAR = 19.679837431231647
+SCHECHTER15_B = [1.9419001265076423, 1.6843806505723544, 1.5003038561471536, 1.3670369833779648,
+                 1.2689219880403695, 1.195126150195898, 1.138155058691824, 1.092823847783893,
+                 1.0555454667701716, 1.023838282880806, 0.9959854257071645, 0.9707991111275014,
+                 0.9474575932996266, 0.9253923629996902, 0.9042101079393786]
+SCHECHTER15_NBAR = [0.0014022274046629074, 0.017877857008321816, 0.10835142812365212, 0.38647319977232125,
+                    0.9463696456518819, 1.7774796502645018, 2.771610849132778, 3.794844809474923,
+                    4.7459183261589715, 5.573165614259365, 6.2647350878662635, 6.831900757373581,
+                    7.295583066943564, 7.678240761551859, 8.0]
+WORKLOADS["schechter128"] = Workload(
+    "schechter128", 128, 750.0, 16, SCHECHTER15_B, SCHECHTER15_NBAR, 0.25, "schechter",
+    n_leapfrog=10, eps_max=0.06, jump=True, jump_leapfrog=10, jump_eps_max=0.15, fixed_bias=6,
+    extra={"M_edges": SCHECHTER15_EDGES, "phi_star": SCHECHTER15_PHI_STAR})
 
 
 def small_workload(N, box=None, n_bins=4, n_sub=1, f_sky=0.5, seed=0, **kw):

@@ -23,13 +23,14 @@ class Problem:
     """A survey plus a starting state, shared by both sides."""
 
     def __init__(self, N, n_sub=1, n_bins=4, f_sky=0.6, seed=3, n_leapfrog=5, eps_max=0.3, jump_leapfrog=4,
-                 jump_eps_max=0.3, box=None, state_scale=0.8, wl=None):
+                 jump_eps_max=0.3, box=None, state_scale=0.8, wl=None, survey=None):
         self.wl = wl or inputs.small_workload(N, box=box, n_bins=n_bins, n_sub=n_sub, f_sky=f_sky, seed=seed,
                                               n_leapfrog=n_leapfrog, eps_max=eps_max,
                                               jump_leapfrog=jump_leapfrog, jump_eps_max=jump_eps_max)
         wl = self.wl
         self.N = wl.N
-        self.delta_true, self.counts, self.R = inputs.make_survey(wl)
+        # survey: (delta_true, counts, R) made elsewhere (e.g. on the device), else the host recipe
+        self.delta_true, self.counts, self.R = survey if survey is not None else inputs.make_survey(wl)
         self.geom = ogrid.Geometry(wl.N, wl.box, wl.n_bins)
         self.P, self.b, self.nbar = inputs.initial_state(wl)
         dh = ogrid.forward(self.delta_true * state_scale)
