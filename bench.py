@@ -178,9 +178,52 @@ def read_traffic():
 
 
 # ---------------------------------------------------------------- oracle (CPU) leg
-def oracle_leapfrog_rate(wl, counts, R, n_steps=2):
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo, else lscpu, else the machine type)."""
+    import platform
+    import subprocess
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
+def host_info():
+    return {"threads_used": 1, "host_cores": os.cpu_count(), "cpu_model": cpu_model(),
+            "note": "the oracle is plain numpy: its FFTs and loops run on one host thread"}
+
+
+def oracle_gibbs_iteration_seconds(name="survey128"):
+    """One full Gibbs iteration (HMC with its leapfrog steps, P draw, jump, b and
+    Nbar draws, rebuild) of the FP64 oracle on the named workload."""
+    from oracle import grid, gibbs
+    from paper_1306_1821_gb300 import inputs
+    wl = inputs.WORKLOADS[name]
+    _, counts, R = inputs.make_survey(wl)
+    geom = grid.Geometry(wl.N, wl.box, wl.n_bins)
+    P, b, nbar = inputs.initial_state(wl)
+    ch = gibbs.Chain(geom, counts, R, P, b, nbar, alpha=wl.alpha, n_leapfrog=wl.n_leapfrog, eps_max=wl.eps_max,
+                     jump=True, jump_leapfrog=wl.jump_leapfrog, jump_eps_max=wl.jump_eps_max,
+                     fixed_bias=wl.fixed_bias, seed=1)
+    t0 = time.perf_counter()
+    ch.iterate()
+    return time.perf_counter() - t0, wl
+
+
+def oracle_leapfrog_rate(wl, counts, R, n_steps=4):
     """The FP64 oracle's leapfrog on host cores: n_steps leapfrog steps of one
-    trajectory (n_steps + 1 force evaluations) at the full workload."""
+    trajectory (n_steps + 1 force evaluations, so the first one is amortised)
+    at the full workload."""
     import numpy as np
 
     from oracle import grid, hmc, model
@@ -204,23 +247,25 @@ def run_reference(args):
     from paper_1306_1821_gb300 import inputs
     wl = inputs.WORKLOADS[WORKLOAD]
     _, counts, R = inputs.make_survey(wl)
-    steps = min(args.steps, 20)
+    steps = min(args.steps, 8)
     warm = min(args.warmup, 1)
+    L = 3
     for _ in range(warm):
         oracle_leapfrog_rate(wl, counts, R, n_steps=1)
     tot = 0.0
     for _ in range(steps):
-        _, dt = oracle_leapfrog_rate(wl, counts, R, n_steps=1)
+        _, dt = oracle_leapfrog_rate(wl, counts, R, n_steps=L)
         tot += dt
-    value = steps / tot
+    value = steps * L / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / (steps * L),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(wl, "cpu"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} single leapfrog steps of one trajectory at 256^3 (2 force "
-                                   f"evaluations each, numpy FP64 FFT, one thread), after {warm} warm-up"},
+                         "sample": f"{steps} trajectories of {L} leapfrog steps ({L + 1} force evaluations each) "
+                                   f"at 256^3 with 6 subsamples, numpy FP64 FFT, one thread, after {warm} "
+                                   f"warm-up", **host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -238,6 +283,44 @@ def config_dict(wl, where):
 
 
 # ---------------------------------------------------------------- GPU leg
+def gpu_mock_timing(s, wl, stream, dev, host_seconds):
+    """The benchmark survey made on the device (Sec. 5 mock: true field, cap x
+    radial response, Poisson counts of every subsample) timed with CUDA events
+    on the library's stream, beside the host recipe's wall time."""
+    import numpy as np
+    import torch
+
+    from paper_1306_1821_gb300 import bps, inputs
+    N, box = wl.N, wl.box
+    n2 = np.arange(3 * (N // 2) ** 2 + 1, dtype=np.float64)
+    P = inputs.true_spectrum(2.0 * np.pi * np.sqrt(n2) / box, N, box)
+    P[0] = 0.0
+    n_r = 4097
+    r = np.arange(n_r) * (box / 2 / (n_r - 1))
+    table = np.broadcast_to(np.exp(-(r / wl.r0) ** 2), (wl.n_sub, n_r)).copy()
+    with torch.cuda.stream(stream):
+        d = torch.empty((N, N, N), dtype=torch.float32, device=dev)
+        Rd = torch.empty((wl.n_sub, N, N, N), dtype=torch.float32, device=dev)
+        c = torch.empty((wl.n_sub, N, N, N), dtype=torch.int32, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    for rep in range(3):
+        e0.record(stream)
+        bps.bps_mock_field(s.ctx, 100 + rep, P, d)
+        bps.bps_mock_response(s.ctx, wl.f_sky, (0.0, 0.0, 1.0), table, Rd)
+        bps.bps_mock_counts(s.ctx, 100 + rep, d, Rd, wl.b, wl.nbar, 0, c)
+        e1.record(stream)
+        stream.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    total = int(c.sum().item())
+    del d, Rd, c
+    return {"gpu_ms": min(ms[1:]), "host_s": host_seconds, "galaxies": total,
+            "what": f"{N}^3 true field, cap x radial response and Poisson counts of {wl.n_sub} subsamples: "
+                    f"on the device (bps_mock_*, CUDA events, best of 2 after one warm-up) and by the host "
+                    f"numpy recipe (inputs.make_survey, wall time)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -256,7 +339,9 @@ def run_ours(args):
     bps.load()
 
     wl = inputs.WORKLOADS[WORKLOAD]
+    t_host = time.perf_counter()
     delta, counts, R = inputs.make_survey(wl, seed=wl.seed + rank)
+    t_host = time.perf_counter() - t_host
     P0, b0, nbar0 = inputs.initial_state(wl)
     stream = torch.cuda.Stream(device=dev)
     s = bps.Sampler(wl.N, wl.box, wl.n_sub, wl.n_bins, stream=stream, n_leapfrog=wl.n_leapfrog,
@@ -270,6 +355,7 @@ def run_ours(args):
     bps.bps_set_data(s.ctx, cnt_d, R_d)
     bps.bps_set_state(s.ctx, d_d, P0, b0, nbar0, 0)
     del cnt_d, R_d, d_d
+    mock_timing = gpu_mock_timing(s, wl, stream, dev, t_host)
 
     # warm-up iterations (also moves the chain off its starting point)
     if args.warmup > 0:
@@ -427,15 +513,23 @@ def run_ours(args):
         }
         if pk is not None:
             line["pk_ess"] = pk
+        line["mock_generation"] = mock_timing
         if stream_ref is not None:
             stream_ref["x_pass_frac_of_this"] = achieved / stream_ref["GBps"]
             line["streaming_reference"] = stream_ref
         if ws == 1 and not args.no_cpu_baseline:
-            v, dt = oracle_leapfrog_rate(wl, counts, R, n_steps=2)
+            v, dt = oracle_leapfrog_rate(wl, counts, R, n_steps=4)
+            git, wl_g = oracle_gibbs_iteration_seconds("survey128")
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"2 leapfrog steps (3 force evaluations) of one trajectory at "
+                                    "sample": f"4 leapfrog steps (5 force evaluations) of one trajectory at "
                                               f"256^3 with 6 subsamples, FP64 numpy on one host thread, "
-                                              f"{dt:.1f} s"}
+                                              f"{dt:.1f} s; plus one full Gibbs iteration at 128^3",
+                                    "s_per_leapfrog": 1.0 / v,
+                                    "s_per_gibbs_iteration_128": git,
+                                    "gibbs_iteration_128": f"{wl_g.name}: {wl_g.N}^3, {wl_g.n_sub} subsamples, "
+                                                           f"{wl_g.n_leapfrog} leapfrog steps, jump on "
+                                                           f"({wl_g.jump_leapfrog} steps)",
+                                    **host_info()}
         print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

@@ -474,6 +474,25 @@ uint64_t bps_kernel_launches(const bps_ctx* ctx);
 bps_status bps_profile(bps_ctx* ctx, int enable);
 bps_status bps_profile_read(bps_ctx* ctx, double* ms, uint64_t* n);
 
+/* Running posterior moments on the device (the paper's posterior analysis,
+ * Secs. 6.2 and 7, Figs. 6-11: ensemble mean and variance maps of the density
+ * field, correlation matrices of P, b and Nbar).  With enable = 1 the sums are
+ * reset and, from then on, every Gibbs iteration of bps_gibbs_iterate adds its
+ * final sample: per voxel delta and delta^2 (FP64, the field transformed to real
+ * space by one extra z pass) and the chain parameters x = (P_0..P_{n_bins-1},
+ * b_0..b_{n_sub-1}, Nbar_0..Nbar_{n_sub-1}) and their products x_i x_j (FP64).
+ * enable = 0 stops adding (the sums are kept).  Uses 16 N^3 + 8 (1 + D + D^2)
+ * bytes of device memory, D = n_bins + 2 n_sub.  Single-chain contexts. */
+bps_status bps_posterior_moments(bps_ctx* ctx, int enable);
+
+/* The moments accumulated so far over n = *n_samples iterations: per voxel
+ * mean_dev = S1 / n and var_dev = S2 / n - mean^2 (double [N][N][N], device;
+ * population moments), param_mean [D] and param_cov [D][D] (host; population
+ * covariance, the order of bps_posterior_moments).  Any output may be NULL.
+ * BPS_ESTATE before bps_posterior_moments or before the first iteration. */
+bps_status bps_posterior_read(bps_ctx* ctx, double* mean_dev, double* var_dev, double* param_mean,
+                              double* param_cov, uint64_t* n_samples);
+
 /* Self-test of failure detection.  Every device wait of the library (the bulk
  * tile copies of the z and fused y/z passes complete on shared-memory
  * mbarriers) is bounded: after 2 s the block gives up, records the timeout in

@@ -104,6 +104,8 @@ _SIGS = {
     "bps_save_chain": ([_P, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "bps_load_chain": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
     "bps_selftest_wait": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "bps_posterior_moments": ([_P, ctypes.c_int], ctypes.c_int),
+    "bps_posterior_read": ([_P, _P, _P, _D, _D, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "bps_mock_field": ([_P, ctypes.c_uint64, _D, _P], ctypes.c_int),
     "bps_mock_counts": ([_P, ctypes.c_uint64, _P, _P, _D, _D, ctypes.c_int, _P], ctypes.c_int),
     "bps_mock_response": ([_P, ctypes.c_double, _D, ctypes.c_int, _D, _P], ctypes.c_int),
@@ -295,6 +297,21 @@ def bps_bias_law(M, b_star=1.2, M_star=-20.83, a=0.895, b=0.105, c=-0.040):
     _check(None, load().bps_bias_law(int(m.size), pm, float(b_star), float(M_star), float(a), float(b), float(c),
                                      out.ctypes.data_as(_D)))
     return out
+
+
+def bps_posterior_moments(ctx, enable=True):
+    _check(ctx, load().bps_posterior_moments(ctx, int(bool(enable))))
+
+
+def bps_posterior_read(ctx, n_bins, n_sub, mean=None, var=None):
+    """(param_mean [D], param_cov [D][D], n); mean / var: optional float64 CUDA tensors [N]^3."""
+    D = n_bins + 2 * n_sub
+    pm = np.zeros(D)
+    pc = np.zeros((D, D))
+    n = ctypes.c_uint64(0)
+    _check(ctx, load().bps_posterior_read(ctx, _dptr(mean), _dptr(var), pm.ctypes.data_as(_D),
+                                          pc.ctypes.data_as(_D), ctypes.byref(n)))
+    return pm, pc, n.value
 
 
 def bps_hmc_step(ctx, want_info=True):

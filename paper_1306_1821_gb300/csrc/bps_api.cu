@@ -100,6 +100,11 @@ struct bps_ctx {
   size_t ev_used[4] = {0, 0, 0, 0};
   double prof_ms[4] = {0, 0, 0, 0};
   uint64_t prof_n[4] = {0, 0, 0, 0};
+  // running posterior moments (bps_posterior_moments): per-voxel sums of delta
+  // and delta^2 [2 N^3], and of the chain parameters [1 + D + D^2], D = n_bins + 2 n_sub
+  bool mom_on = false;
+  double* mom = nullptr;
+  double* pmom = nullptr;
   // device table of the mock calls (amplitudes, selection), grown on demand
   void* mock_buf = nullptr;
   size_t mock_bytes = 0;
@@ -540,6 +545,13 @@ bps_status gibbs_once(bps_ctx* ctx, double* rec, int rec_len, long long iter_str
   if (st == BPS_OK && jump) st = jump_stage(ctx, false, true);
   if (st == BPS_OK) st = bias_stage(ctx, false);
   if (st != BPS_OK) return st;
+  if (ctx->mom_on) {
+    // running posterior moments of this iteration's sample: W holds the x and y
+    // inverse transforms of the field (bias stage), so one z pass gives delta
+    ctx->pt.z_mom(fields_at(ctx, 0), ctx->mom, ctx->stream);
+    launch_param_moments(scalars_at(ctx, 0), ctx->pmom, ctx->stream);
+    LAUNCHED(ctx, 2);
+  }
   launch_record(scalars(ctx), rec, rec_len, iter_stride, ctx->chain_id.empty() ? 0 : ctx->chain_id[0], ctx->batch,
                 ctx->stream);
   launch_advance(ctx->ds, ctx->batch, ctx->stream);
@@ -619,6 +631,9 @@ void free_streams(bps_ctx* c) {
 }
 
 void free_all(bps_ctx* c) {
+  if (c->mom) cudaFree(c->mom);
+  if (c->pmom) cudaFree(c->pmom);
+  c->mom = c->pmom = nullptr;
   if (c->mock_buf) cudaFree(c->mock_buf);
   c->mock_buf = nullptr;
   drop_graph(c);
@@ -1553,6 +1568,54 @@ bps_status bps_mock_response(bps_ctx* ctx, double f_sky, const double* axis, int
   if (st != BPS_OK) return st;
   if (!axis || !table || !R_dev) return fail(ctx, BPS_EINVAL, "null argument");
   return mock_result(ctx, mock_response(v, f_sky, axis, n_r, table, R_dev));
+}
+
+// ---- posterior analysis (Secs. 6.2 and 7)
+bps_status bps_posterior_moments(bps_ctx* ctx, int enable) {
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "null argument or batch context");
+  if (enable) {
+    const size_t D = (size_t)ctx->cfg.n_bins + 2 * (size_t)ctx->nsub[0];
+    const size_t nm = 2 * (size_t)ctx->nv, np = 1 + D + D * D;
+    if (!ctx->mom && cudaMalloc(&ctx->mom, nm * sizeof(double)) != cudaSuccess) {
+      ctx->mom = nullptr;
+      return fail(ctx, BPS_ENOMEM, "posterior moment buffers");
+    }
+    if (!ctx->pmom && cudaMalloc(&ctx->pmom, np * sizeof(double)) != cudaSuccess) {
+      ctx->pmom = nullptr;
+      return fail(ctx, BPS_ENOMEM, "posterior moment buffers");
+    }
+    CK(cudaMemsetAsync(ctx->mom, 0, nm * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(ctx->pmom, 0, np * sizeof(double), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if ((enable != 0) != ctx->mom_on) drop_graph(ctx);   // the iteration's launches change
+  ctx->mom_on = enable != 0;
+  return BPS_OK;
+}
+
+bps_status bps_posterior_read(bps_ctx* ctx, double* mean_dev, double* var_dev, double* param_mean,
+                              double* param_cov, uint64_t* n_samples) {
+  if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "null argument or batch context");
+  if (!ctx->mom || !ctx->pmom) return fail(ctx, BPS_ESTATE, "bps_posterior_moments has not been enabled");
+  const size_t D = (size_t)ctx->cfg.n_bins + 2 * (size_t)ctx->nsub[0];
+  std::vector<double> acc(1 + D + D * D);
+  CK(cudaMemcpyAsync(acc.data(), ctx->pmom, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const double n = acc[0];
+  if (n_samples) *n_samples = (uint64_t)n;
+  if (!(n > 0.0)) return fail(ctx, BPS_ESTATE, "no Gibbs iteration has been accumulated yet");
+  if (mean_dev || var_dev) {
+    launch_moments_finish(ctx->mom, ctx->nv, n, mean_dev, var_dev, ctx->n_sm * 8, ctx->stream);
+    LAUNCHED(ctx, 1);
+  }
+  for (size_t i = 0; i < D; ++i) {
+    const double mi = acc[1 + i] / n;
+    if (param_mean) param_mean[i] = mi;
+    if (param_cov)
+      for (size_t j = 0; j < D; ++j) param_cov[i * D + j] = acc[1 + D + i * D + j] / n - mi * (acc[1 + j] / n);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BPS_OK;
 }
 
 bps_status bps_selftest_wait(bps_ctx* ctx, uint64_t limit_ns) {

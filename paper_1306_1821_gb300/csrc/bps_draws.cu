@@ -543,6 +543,40 @@ void launch_mstat(const ScalarArgs& a, int region, int nblk, int n_mass, int fin
 }
 
 
+// ------------------------------------------------------------------ posterior moments
+// Running sums of the chain parameters of one chain (Secs. 6.2 and 7: the
+// correlation matrices of P, b and Nbar), one FP64 accumulation per Gibbs
+// iteration, in a fixed order.
+__global__ void k_param_moments(ScalarArgs a, double* acc) {
+  const DevState* ds = a.ds;
+  const int nb = a.n_bins, ns = ds->nsub, D = nb + 2 * ns;
+  __shared__ double x[MAXB + 2 * MAXS];
+  for (int i = threadIdx.x; i < D; i += blockDim.x)
+    x[i] = i < nb ? ds->P[i] : i < nb + ns ? ds->b[i - nb] : ds->nbar[i - nb - ns];
+  __syncthreads();
+  if (threadIdx.x == 0) acc[0] += 1.0;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) acc[1 + i] += x[i];
+  for (int q = threadIdx.x; q < D * D; q += blockDim.x) acc[1 + D + q] += x[q / D] * x[q % D];
+}
+
+// mean = S1 / n, var = S2 / n - mean^2 per voxel (population moments)
+__global__ void k_moments_finish(const double* __restrict__ mom, long long nv, double n, double* mean, double* var) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+    const double m = mom[i] / n;
+    if (mean) mean[i] = m;
+    if (var) var[i] = mom[nv + i] / n - m * m;
+  }
+}
+
+void launch_moments_finish(const double* mom, long long nv, double n, double* mean, double* var, int blocks,
+                           cudaStream_t s) {
+  k_moments_finish<<<blocks, 256, 0, s>>>(mom, nv, n, mean, var);
+}
+
+void launch_param_moments(const ScalarArgs& a, double* acc, cudaStream_t s) {
+  k_param_moments<<<1, 256, 0, s>>>(a, acc);
+}
+
 // ------------------------------------------------------------------ failure detection
 // Self-test of the bounded device waits: one thread announces 16 bytes on a
 // shared-memory mbarrier and waits for them, but no copy is ever issued, so the

@@ -36,6 +36,8 @@ struct PassTable {
   void (*z_noise)(const Fields&, int nch, cudaStream_t);
   void (*z_r2c)(const Fields&, const float* rin, float2* dst, cudaStream_t);   // one chain
   void (*z_c2r)(const Fields&, const float2* src, float* rout, cudaStream_t);  // one chain
+  // one chain: delta = C2R_z(W) added to the running sums mom[0..N^3) (delta) and mom[N^3..) (delta^2)
+  void (*z_mom)(const Fields&, double* mom, cudaStream_t);
   void (*z_sums)(const Fields&, int region, int nch, cudaStream_t);
   // z_grad with 4, 8 or 16 line pairs per tile (autotuned per grid) and the
   // number of tiles (likelihood-energy partials) of each
@@ -94,6 +96,12 @@ void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, doub
 void launch_record(const ScalarArgs& a, double* rec_dev, int rec_len, long long iter_stride, int chain0, int nch,
                    cudaStream_t s);
 void launch_advance(DevState* ds, int nch, cudaStream_t s);
+// running sums of the chain parameters x = (P, b, Nbar) of one chain: acc[0] += 1,
+// acc[1 + i] += x_i, acc[1 + D + i D + j] += x_i x_j, D = n_bins + 2 nsub
+void launch_param_moments(const ScalarArgs& a, double* acc, cudaStream_t s);
+// per voxel mean = mom[i] / n and var = mom[nv + i] / n - mean^2 (either output may be NULL)
+void launch_moments_finish(const double* mom, long long nv, double n, double* mean, double* var, int blocks,
+                           cudaStream_t s);
 // activate an uploaded survey: data constants from the data kernel's partials
 // (4 x nblk per subsample, chains cstride apart) and DevState::dslot = slot, or
 // ST_BADDATA for invalid data

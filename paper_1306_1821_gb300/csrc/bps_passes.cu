@@ -51,6 +51,9 @@ struct ZArgs {
   float* rout;
   int region;
   uint64_t seed;
+  // Z_C2R with mom: instead of writing delta, add delta and delta^2 to the
+  // running sums mom[0..N^3) and mom[N^3..2 N^3) (FP64; posterior moments)
+  double* mom = nullptr;
 };
 
 // ------------------------------------------------------------------ x pass helpers
@@ -716,11 +719,24 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
     const long long la = (L0 + 2 * f) * N, lb = la + N;
     if constexpr (MODE == Z_C2R) {
       if (f < LP) {
+        if (za.mom) {
+          const long long nv3 = (long long)N * N * N;
 #pragma unroll
-        for (int d = 0; d < R2; ++d) {
-          const int n = c + R1 * d;
-          za.rout[la + n] = v[d].x * fp.inv_nv;
-          za.rout[lb + n] = v[d].y * fp.inv_nv;
+          for (int d = 0; d < R2; ++d) {
+            const int n = c + R1 * d;
+            const double da = (double)(v[d].x * fp.inv_nv), db = (double)(v[d].y * fp.inv_nv);
+            za.mom[la + n] += da;
+            za.mom[lb + n] += db;
+            za.mom[nv3 + la + n] += da * da;
+            za.mom[nv3 + lb + n] += db * db;
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < R2; ++d) {
+            const int n = c + R1 * d;
+            za.rout[la + n] = v[d].x * fp.inv_nv;
+            za.rout[lb + n] = v[d].y * fp.inv_nv;
+          }
         }
       }
       return;
@@ -1032,6 +1048,7 @@ static PassTable make_table() {
   T.z_noise = [](const Fields& f, int n, cudaStream_t s) { L::template z<Z_NOISE>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, -1, 0}, n, s); };
   T.z_r2c = [](const Fields& f, const float* rin, float2* dst, cudaStream_t s) { L::template z<Z_R2C>(f, ZArgs{nullptr, dst, rin, nullptr, -1, 0}, 1, s); };
   T.z_c2r = [](const Fields& f, const float2* src, float* rout, cudaStream_t s) { L::template z<Z_C2R>(f, ZArgs{src, nullptr, nullptr, rout, -1, 0}, 1, s); };
+  T.z_mom = [](const Fields& f, double* mom, cudaStream_t s) { L::template z<Z_C2R>(f, ZArgs{f.W, nullptr, nullptr, nullptr, -1, 0, mom}, 1, s); };
   T.z_sums = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_SUMS>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
   return T;
 }
