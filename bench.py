@@ -612,12 +612,25 @@ def pk_ess(rec, n_bins, N, secs):
 
     from paper_1306_1821_gb300 import diagnostics
     P = rec[:, :n_bins]
-    ess = np.array([diagnostics.ess_geyer(np.log(P[:, m])) for m in range(n_bins)])
+    lnP = np.log(P)
+    ess = np.array([diagnostics.ess_geyer(lnP[:, m]) for m in range(n_bins)])
     inside = [m for m in range(n_bins) if (m + 1) * math.sqrt(3.0) * N / 2 / n_bins <= N / 2]
+    # standard error of each bin's ESS from four consecutive quarters of the
+    # chain (their ESS summed estimates the whole chain's; the spread of the
+    # quarters gives its error); an ESS below ~50 is itself poorly determined
+    q = len(rec) // 4
+    seg = np.array([[diagnostics.ess_geyer(lnP[i * q:(i + 1) * q, m]) for i in range(4)] for m in range(n_bins)])
+    ess_se = 2.0 * seg.std(1, ddof=1)
+    m_min = inside[int(np.argmin(ess[inside]))]
     return {"ess_per_bin": [round(float(e), 1) for e in ess],
+            "ess_se_per_bin": [round(float(e), 1) for e in ess_se],
             "bins_inside_nyquist": inside,
             "min_ess_per_s": float(ess[inside].min() / secs),
+            "min_ess_bin": int(m_min), "min_ess": float(ess[m_min]), "min_ess_se": float(ess_se[m_min]),
+            "min_ess_reliable": bool(ess[m_min] >= 50.0),
             "median_ess_per_s": float(np.median(ess[inside]) / secs),
+            "correlation_length_median": float(np.median([diagnostics.correlation_length(lnP[:, m])
+                                                          for m in inside])),
             "iterations": int(len(rec)), "seconds": secs,
             "mean_lnP": [round(float(v), 4) for v in np.log(P).mean(0)],
             "sd_lnP": [round(float(v), 4) for v in np.log(P).std(0)]}
@@ -730,7 +743,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96", "precond128", "precond256"])
     ap.add_argument("--ess-iters", type=int, default=None,
-                    help="Gibbs iterations of the P(k) ESS run (default 2000 at 256^3, 20000 per arm of precond128; "
+                    help="Gibbs iterations of the P(k) ESS run (default 4000 at 256^3, 20000 per arm of precond128; "
                          "0 skips it)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
@@ -744,7 +757,7 @@ def main(argv=None):
             args.ess_iters = 20000
         return run_precond(args)
     if args.ess_iters is None:
-        args.ess_iters = 2000
+        args.ess_iters = 4000
     return run_ours(args)
 
 
