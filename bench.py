@@ -579,6 +579,8 @@ def run_batch(args):
     secs = e0.elapsed_time(e1) / 1000.0
     launches = bps.bps_kernel_launches(batch) - l0
     vox = sum(w.N ** 3 for w in wls)
+    per_iter = launches / max(args.steps, 1)
+    floor_us = graph_node_floor_us(stream, int(round(per_iter)))
     acc = float(np.mean([rec[:, bps.bps_batch_record_slot(batch, j), 16 + 2 * w.n_sub + 1]
                          for j, w in enumerate(wls)]))
     line = {
@@ -595,12 +597,40 @@ def run_batch(args):
         "gibbs_iterations_per_s": len(wls) * args.steps / secs,
         "hmc_acceptance": acc,
         "gpu_launches": int(launches),
+        "launch_floor": {"kernels_per_iteration": per_iter, "us_per_graph_node": floor_us,
+                         "share_of_iteration": per_iter * floor_us / (1000.0 * 1000.0 * secs / args.steps),
+                         "what": "replay time per node of a CUDA graph of as many trivial kernels as one batch "
+                                 "iteration launches (torch fill of one element): the most a single persistent "
+                                 "kernel could save by removing the launches"},
         "setup_s": setup_s,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     bps.bps_destroy(batch)
     return 0
+
+
+def graph_node_floor_us(stream, n_nodes, reps=20):
+    """Microseconds per node of a captured graph of n_nodes trivial kernels."""
+    import torch
+    x = torch.zeros(1, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        x.fill_(0.0)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(n_nodes):
+                x.fill_(1.0)
+        g.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return 1000.0 * e0.elapsed_time(e1) / (reps * max(n_nodes, 1))
 
 
 # ---------------------------------------------------------------- learned mass vs plain
@@ -639,19 +669,22 @@ def pk_ess(rec, n_bins, N, secs):
 DAMPED = 0.6          # damping of the second network arm (it learns 0.6 ln s)
 PRECOND_RUNS = {
     # workload: (survey, training surveys, mass bins)
-    "precond128": ("survey128", 64, 64),
-    "precond256": ("survey256", 32, 64),
+    "precond128": ("survey128", 5000, 64),
+    "precond256": ("survey256", 256, 64),
 }
 
 
 def run_precond(args):
     """P(k) effective samples per second of the full sampler with the plain
-    diagonal mass and with the trained network mass, on the 128^3 survey
-    (precond128) or the 256^3 survey of the headline (precond256).  The network
+    diagonal mass and with the trained network mass (gamma = 1, and damped to
+    gamma = 0.6), on the 128^3 survey (precond128) or the 256^3 survey of the
+    headline (precond256), over several seeds per arm.  The network
     (2 n_bins -> 128 -> 128 -> 64, BF16 operands) is trained on the device on
-    statistics of random surveys of the same recipe (random caps and spectra),
-    in two rounds (the second on chains that already move with the first
-    round's mass); the benchmark survey itself is held out."""
+    statistics of plain chains on random surveys of the same recipe (random caps
+    and spectra), made on the device; the benchmark survey itself is held out.
+    Equal accuracy: the per-bin posterior means of ln P of each network arm and
+    the plain arm, pooled over seeds, must agree within three combined Monte
+    Carlo standard errors (reported as the largest z)."""
     import numpy as np
     import torch
 
@@ -660,35 +693,150 @@ def run_precond(args):
         from paper_1306_1821_gb300 import build as b
         b.build()
     bps.load()
-    survey, n_train, n_mass = PRECOND_RUNS[args.workload]
+    survey, n_train_default, n_mass = PRECOND_RUNS[args.workload]
+    n_train = args.train_examples or n_train_default
     wl = inputs.WORKLOADS[survey]
     jeps = 0.15
     t0 = time.time()
     probs = precond.random_problems(wl, n_train, 5000, p_jitter=0.3)
-    F, T = precond.measure(probs, n_mass, n_moves=300, burn_in=100)
-    pc = precond.Preconditioner(F.shape[1], n_mass)
-    pc.fit(F, T, steps=2000, batch=64)
-    F2, T2 = precond.measure(probs, n_mass, n_moves=300, burn_in=100, sampler_mass=pc)
-    pc2 = precond.Preconditioner(F.shape[1], n_mass, seed=1)
-    loss = pc2.fit(F2, T2, steps=2000, batch=64)
-    pc3 = precond.Preconditioner(F.shape[1], n_mass, seed=1)
-    pc3.fit(F2, T2, steps=2000, batch=64, damping=DAMPED)
+    # chains per batch context: ~200 MB each at 128^3, ~1.6 GB at 256^3
+    F, T = precond.measure(probs, n_mass, n_moves=args.stat_moves, burn_in=100, device_mocks=True,
+                           chunk=256 if wl.N <= 128 else 48)
+    t_stats = time.time() - t0
+    nets = {}
+    for arm, gamma in (("network", 1.0), ("network_damped", DAMPED)):
+        pc = precond.Preconditioner(F.shape[1], n_mass, seed=1)
+        loss = pc.fit(F, T, steps=4000, batch=128, damping=gamma)
+        nets[arm] = (pc, loss)
     train_s = time.time() - t0
     delta, counts, R = inputs.make_survey(wl)
     P0, b0, n0 = inputs.initial_state(wl)
     cnt = torch.from_numpy(counts).cuda()
     Rt = torch.from_numpy(R).cuda()
     d32 = torch.from_numpy(delta.astype(np.float32)).cuda()
-    arms = {}
-    for arm in ("plain", "network", "network_damped"):
-        s = bps.Sampler(wl.N, wl.box, wl.n_sub, wl.n_bins, n_leapfrog=wl.n_leapfrog, eps_max=wl.eps_max, jump=1,
-                        jump_leapfrog=10, jump_eps_max=jeps, fixed_bias_index=0, seed=3)
-        bps.bps_set_data(s.ctx, cnt, Rt)
-        bps.bps_set_state(s.ctx, d32, P0, b0, n0, 0)
-        if arm == "network":
-            pc2.install(s.ctx)
-        elif arm == "network_damped":
-            pc3.install(s.ctx)
+    arms = {a: [] for a in ("plain", "network", "network_damped")}
+    lnPs = {a: [] for a in arms}
+    for k in range(args.seeds):
+        for arm in arms:
+            s = bps.Sampler(wl.N, wl.box, wl.n_sub, wl.n_bins, n_leapfrog=wl.n_leapfrog, eps_max=wl.eps_max,
+                            jump=1, jump_leapfrog=10, jump_eps_max=jeps, fixed_bias_index=0, seed=3 + 101 * k)
+            bps.bps_set_data(s.ctx, cnt, Rt)
+            bps.bps_set_state(s.ctx, d32, P0, b0, n0, 0)
+            if arm != "plain":
+                nets[arm][0].install(s.ctx)
+            bps.bps_gibbs_iterate(s.ctx, max(args.warmup, 300))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            rec = bps.bps_gibbs_iterate(s.ctx, args.ess_iters, s.rec_len)
+            e1.record()
+            torch.cuda.synchronize()
+            secs = e0.elapsed_time(e1) / 1000.0
+            r = pk_ess(rec, wl.n_bins, wl.N, secs)
+            r["hmc_acceptance"] = float(np.mean(rec[:, -1]))
+            r["ms_per_iteration"] = 1000.0 * secs / args.ess_iters
+            r["seed"] = 3 + 101 * k
+            s.close()
+            arms[arm].append(r)
+            lnPs[arm].append(np.log(rec[:, :wl.n_bins]))
+    inside = arms["plain"][0]["bins_inside_nyquist"]
+
+    def stats(vals):
+        v = np.asarray(vals, dtype=np.float64)
+        se = float(v.std(ddof=1) / math.sqrt(len(v))) if len(v) > 1 else None
+        return {"per_seed": [round(float(x), 4) for x in v], "mean": float(v.mean()), "se": se}
+
+    summary = {}
+    for arm in arms:
+        summary[arm] = {"min_ess_per_s": stats([r["min_ess_per_s"] for r in arms[arm]]),
+                        "median_ess_per_s": stats([r["median_ess_per_s"] for r in arms[arm]]),
+                        "hmc_acceptance": stats([r["hmc_acceptance"] for r in arms[arm]]),
+                        "ms_per_iteration": stats([r["ms_per_iteration"] for r in arms[arm]])}
+    ratios, accuracy = {}, {}
+    for arm in ("network", "network_damped"):
+        ratios[arm] = {
+            "min_ess_per_s": stats([a["min_ess_per_s"] / p["min_ess_per_s"] for a, p in zip(arms[arm], arms["plain"])]),
+            "median_ess_per_s": stats([a["median_ess_per_s"] / p["median_ess_per_s"]
+                                       for a, p in zip(arms[arm], arms["plain"])])}
+        # equal accuracy, pooled over seeds: per-bin posterior means of ln P
+        za = []
+        for m in inside:
+            mu = [np.mean([x[:, m].mean() for x in lnPs[a]]) for a in (arm, "plain")]
+            sd = np.mean([x[:, m].std() for x in lnPs["plain"]])
+            ess = [np.sum([r["ess_per_bin"][m] for r in arms[a]]) for a in (arm, "plain")]
+            za.append(abs(mu[0] - mu[1]) / (sd * math.sqrt(1.0 / max(ess[0], 1.0) + 1.0 / max(ess[1], 1.0))))
+        accuracy[arm] = {"max_z_over_bins": float(np.max(za)), "bins_over_3": int(np.sum(np.array(za) > 3.0))}
+    line = {
+        "metric": "P(k) effective samples/s, learned mass vs plain diagonal mass (min over bins inside the "
+                  "Nyquist sphere)",
+        "value": summary["network"]["min_ess_per_s"]["mean"],
+        "unit": "effective samples/s",
+        "n_gpus": 1, "steps": args.ess_iters, "warmup": max(args.warmup, 300),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
+        "data": "synthetic",
+        "config": {"workload": f"{wl.name}: {wl.N}^3 grid, L={wl.box:g} Mpc/h, {wl.n_sub} subsamples, "
+                               f"{wl.f_sky:.0%} sky, {wl.radial} radial selection, {wl.n_bins} k bins, "
+                               f"{wl.n_leapfrog} leapfrog steps (eps_max {wl.eps_max}), jump on (10 steps, "
+                               f"eps_max {jeps}); network {2 * wl.n_bins}-128-128-{n_mass} trained on {len(F)} "
+                               f"(feature, target) pairs from plain chains ({args.stat_moves} HMC moves each) on "
+                               "random surveys of the same recipe made on the device; the survey itself held out; "
+                               f"{args.seeds} seeds x {args.ess_iters} iterations per arm"},
+        "summary": summary, "ratio_to_plain": ratios, "equal_accuracy": accuracy,
+        "damping_of_network_damped": DAMPED,
+        "per_seed": arms,
+        "training": {"seconds": train_s, "statistics_seconds": t_stats, "examples": int(len(F)),
+                     "final_minibatch_loss": {a: nets[a][1] for a in nets}},
+    }
+    print(json.dumps(line), flush=True)
+    for a in nets:
+        nets[a][0].close()
+    return 0
+
+
+def run_schechter(args):
+    """Gibbs iterations per second on the paper's own setup (Sec. 5): 128^3, L =
+    750 Mpc/h, fifteen luminosity subsamples with the Schechter selection, the
+    mean numbers per magnitude bin and the luminosity bias law, a 25% cap; the
+    survey is made on the device (bps_mock_*).  Beside it, the same sampler on
+    the six-subsample 128^3 survey, to show what the nine extra subsamples cost
+    (the a, c rebuild and the bias and normalisation sums grow with n_sub; the
+    leapfrog does not)."""
+    import numpy as np
+    import torch
+
+    from paper_1306_1821_gb300 import bps, inputs
+    if not os.path.exists(bps.LIB_PATH):
+        from paper_1306_1821_gb300 import build as b
+        b.build()
+    bps.load()
+    out = {}
+    for name in ("schechter128", "survey128"):
+        wl = inputs.WORKLOADS[name]
+        N, box = wl.N, wl.box
+        mock = bps.Sampler(N, box, wl.n_sub, wl.n_bins)
+        n2 = np.arange(3 * (N // 2) ** 2 + 1, dtype=np.float64)
+        Pk = inputs.true_spectrum(2.0 * np.pi * np.sqrt(n2) / box, N, box)
+        Pk[0] = 0.0
+        if wl.radial == "schechter":
+            table, _ = bps.bps_schechter_tables(np.asarray(wl.extra["M_edges"]), box / 2, 4097)
+        else:
+            r = np.arange(4097) * (box / 2 / 4096)
+            table = np.broadcast_to(np.exp(-(r / wl.r0) ** 2), (wl.n_sub, 4097)).copy()
+        d = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+        R = torch.empty((wl.n_sub, N, N, N), dtype=torch.float32, device="cuda")
+        c = torch.empty((wl.n_sub, N, N, N), dtype=torch.int32, device="cuda")
+        bps.bps_mock_field(mock.ctx, 9, Pk, d)
+        bps.bps_mock_response(mock.ctx, wl.f_sky, (0.0, 0.0, 1.0), table, R)
+        bps.bps_mock_counts(mock.ctx, 9, d, R, wl.b, wl.nbar, 0, c)
+        torch.cuda.synchronize()
+        mock.close()
+        P0, b0, n0 = inputs.initial_state(wl)
+        s = bps.Sampler(N, box, wl.n_sub, wl.n_bins, n_leapfrog=wl.n_leapfrog, eps_max=wl.eps_max, jump=1,
+                        jump_leapfrog=wl.jump_leapfrog, jump_eps_max=0.15, fixed_bias_index=wl.fixed_bias, seed=2)
+        bps.bps_set_data(s.ctx, c, R)
+        bps.bps_set_state(s.ctx, d, P0, b0, n0, 0)
+        del c, R, d
         bps.bps_gibbs_iterate(s.ctx, max(args.warmup, 300))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -698,39 +846,25 @@ def run_precond(args):
         e1.record()
         torch.cuda.synchronize()
         secs = e0.elapsed_time(e1) / 1000.0
-        r = pk_ess(rec, wl.n_bins, wl.N, secs)
-        r["hmc_acceptance"] = float(np.mean(rec[:, -1]))
-        r["ms_per_iteration"] = 1000.0 * secs / args.ess_iters
-        if arm != "plain":
-            r["mass_scales_in_use"] = [round(float(v), 3) for v in bps.bps_get_mass_scale(s.ctx)]
+        r = pk_ess(rec, wl.n_bins, N, secs)
+        r.update({"n_sub": wl.n_sub, "gibbs_iterations_per_s": args.ess_iters / secs,
+                  "ms_per_iteration": 1000.0 * secs / args.ess_iters,
+                  "leapfrog_steps_per_s": args.ess_iters * wl.n_leapfrog / secs,
+                  "hmc_acceptance": float(np.mean(rec[:, -1])),
+                  "mean_b": [round(float(v), 4) for v in rec[:, wl.n_bins:wl.n_bins + wl.n_sub].mean(0)],
+                  "true_b": [round(float(v), 4) for v in wl.b]})
         s.close()
-        arms[arm] = r
-    line = {
-        "metric": "P(k) effective samples/s, learned mass vs plain diagonal mass (min over bins inside the "
-                  "Nyquist sphere)",
-        "value": arms["network"]["min_ess_per_s"],
-        "unit": "effective samples/s",
-        "n_gpus": 1, "steps": args.ess_iters, "warmup": max(args.warmup, 300),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
-        "data": "synthetic",
-        "config": {"workload": f"{wl.name}: {wl.N}^3 grid, L={wl.box:g} Mpc/h, {wl.n_sub} subsamples, "
-                               f"{wl.f_sky:.0%} sky, {wl.radial} radial selection, {wl.n_bins} k bins, "
-                               f"{wl.n_leapfrog} leapfrog steps (eps_max {wl.eps_max}), jump on (10 steps, "
-                               f"eps_max {jeps}); network {2 * wl.n_bins}-128-128-{n_mass} trained on {n_train} "
-                               "random surveys of the same recipe, the survey itself held out"},
-        "plain": arms["plain"], "network": arms["network"], "network_damped": arms["network_damped"],
-        "damping_of_network_damped": DAMPED,
-        "ratio_min_ess_per_s": arms["network"]["min_ess_per_s"] / arms["plain"]["min_ess_per_s"],
-        "ratio_median_ess_per_s": arms["network"]["median_ess_per_s"] / arms["plain"]["median_ess_per_s"],
-        "ratio_damped_min_ess_per_s": arms["network_damped"]["min_ess_per_s"] / arms["plain"]["min_ess_per_s"],
-        "ratio_damped_median_ess_per_s": (arms["network_damped"]["median_ess_per_s"]
-                                          / arms["plain"]["median_ess_per_s"]),
-        "training": {"seconds": train_s, "examples": int(2 * len(F)), "final_minibatch_loss": loss},
-    }
+        out[name] = r
+    line = {"metric": "Gibbs iterations/s on the paper's fifteen-subsample setup (Sec. 5)",
+            "value": out["schechter128"]["gibbs_iterations_per_s"], "unit": "Gibbs iterations/s",
+            "n_gpus": 1, "steps": args.ess_iters, "warmup": max(args.warmup, 300), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (made on the device)",
+            "config": {"workload": "schechter128: 128^3, L=750 Mpc/h, 15 subsamples (M from -23 to -17 in 0.4 "
+                                   "bins), Schechter selection in 14.5 < r < 17.77, bias law Eq. rel_bias, 25% cap, "
+                                   "16 k bins, 10 leapfrog steps, jump on (10 steps); beside it survey128 "
+                                   "(6 subsamples)"},
+            "schechter128": out["schechter128"], "survey128": out["survey128"]}
     print(json.dumps(line), flush=True)
-    pc.close()
-    pc2.close()
-    pc3.close()
     return 0
 
 
@@ -741,7 +875,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch96", "precond128", "precond256"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batch96", "precond128", "precond256", "schechter128"])
+    ap.add_argument("--train-examples", type=int, default=None,
+                    help="(feature, target) pairs of the preconditioner training set (precond* workloads)")
+    ap.add_argument("--stat-moves", type=int, default=300, help="HMC moves per training statistic (precond*)")
+    ap.add_argument("--seeds", type=int, default=3, help="chain seeds per arm (precond*)")
     ap.add_argument("--ess-iters", type=int, default=None,
                     help="Gibbs iterations of the P(k) ESS run (default 4000 at 256^3, 20000 per arm of precond128; "
                          "0 skips it)")
@@ -756,6 +895,10 @@ def main(argv=None):
         if args.ess_iters is None:
             args.ess_iters = 20000
         return run_precond(args)
+    if args.workload == "schechter128":
+        if args.ess_iters is None:
+            args.ess_iters = 4000
+        return run_schechter(args)
     if args.ess_iters is None:
         args.ess_iters = 4000
     return run_ours(args)

@@ -67,6 +67,9 @@ struct bps_ctx {
   int zgrad_tiles = 0;
   int zgrad_pairs = 8;
   YzEntry yz{};                 // fused y^-1 / z / y stage (run == nullptr: three passes)
+  // leapfrog x pass with tensor-copy staged tiles (nullptr: the direct-load pass)
+  XLeapTma xleap = nullptr;
+  XMaps xmaps{};
   MassNet* mnet = nullptr;      // network mass (bps_set_mass_net): scales recomputed before every move
   std::vector<char> have_data;
   int rebuild_blocks = 0;
@@ -435,6 +438,7 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   for (int st = 1; st <= L; ++st) {
     prof_mark(ctx, 0);
     if (st == 1) P.x_leapg(f, region_offset(ctx, RG_INIT) + 2 * ctx->part_stride, B, s);
+    else if (ctx->xleap) ctx->xleap(f, ctx->xmaps, 0, B, s);
     else P.x_leap(f, 0, B, s);
     prof_mark(ctx, 0);
     sf = force_stage(ctx, f, st == L ? region_offset(ctx, RG_LIK1) : -1, true, s);
@@ -892,6 +896,17 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
     free_all(ctx);
     delete ctx;
     return fail(nullptr, BPS_ECUDA, msg);
+  }
+  // the leapfrog x pass with its tiles staged by tensor copies (BPS_XTMA = 1, 2
+  // or 3: which tiles, see xleap_tma) where the driver offers the tensor-map
+  // encoder; by default the direct-load pass
+  {
+    const char* xe = std::getenv("BPS_XTMA");
+    const int which = xe ? std::atoi(xe) : 0;
+    if (which > 0) {
+      ctx->xleap = xleap_tma(grid_n, which);
+      if (ctx->xleap && !make_xmaps(fields(ctx), grid_n, B, &ctx->xmaps)) ctx->xleap = nullptr;
+    }
   }
   if (choose_zgrad(ctx) != BPS_OK) {
     std::string msg = "tile autotuning failed: " + ctx->err;

@@ -1,6 +1,7 @@
 // Internal interfaces between the translation units of the bps library.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "bps_common.cuh"
@@ -46,6 +47,20 @@ struct PassTable {
 };
 
 bool pass_table(int N, PassTable* out);
+
+// Tensor maps of the half spectra of a group (4D: kz, ky, kx, chain; 8-byte
+// elements) for the TMA-staged leapfrog x pass; box 16 (or F) columns x 1 x N
+// rows x 1 chain.  ok = false when the driver offers no tensor-map encoder.
+struct XMaps {
+  CUtensorMap W, d0, d1, ph;
+  bool ok = false;
+};
+bool make_xmaps(const Fields& f, int N, int nch, XMaps* out);
+// the leapfrog x pass with its tiles staged by tensor copies (first: the first
+// kick of a trajectory); nullptr where a grid has none
+using XLeapTma = void (*)(const Fields&, const XMaps&, int first, int nch, cudaStream_t);
+// which: 1 stages W, delta and p; 2 W and delta; 3 W only (0 or other: none)
+XLeapTma xleap_tma(int N, int which);
 
 // The fused y^-1 / z / y stage of a force evaluation (bps_yz.cu): one CTA per
 // x plane holds the plane in shared memory, so W is read and written once.

@@ -12,6 +12,7 @@
 #include "bps_internal.h"
 #include "bps_passes.cuh"
 #include "bps_tma.cuh"
+#include <cudaTypedefs.h>
 
 namespace bps {
 
@@ -504,6 +505,147 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
       fp.part[xa.region + m * fp.part_stride + blockIdx.x] = sum;
     }
     return;
+  }
+}
+
+// ------------------------------------------------------------------ TMA-staged leapfrog x pass
+// The leapfrog x pass (X_LEAP: FFT_x(W) -> force, kick, drift, IFFT_x -> W) with
+// its three input tiles staged in shared memory before any arithmetic: for a
+// regular tile one thread issues tensor copies of the W, delta and p tiles
+// (N rows x F columns each; rows are kx, N ZP elements apart) on one mbarrier,
+// so all of the tile's loads are in flight at once and no thread spends issue
+// slots or registers on them; a Nyquist tile (columns are ky rows, one element
+// per row) is loaded by the threads.  Stores go straight from registers.  The
+// W tile lands in the buffer the transform exchanges through.
+// SD, SP: the delta and p tiles are staged too (else read straight from HBM in
+// the kick); staging all three holds 96 KB per block at 256^3, two blocks per SM.
+template <int N, int SD, int SP>
+struct XTma {
+  using C = Cfg<N>;
+  static constexpr int TILE = N * C::F;                    // complex elements of one tile
+  static constexpr size_t SMEM = (1 + SD + SP) * (size_t)TILE * sizeof(float2);
+  static constexpr int MIN_BLOCKS = SD + SP == 2 ? 2 : 3;
+};
+
+template <int N, int SD, int SP>
+__global__ void __launch_bounds__(Cfg<N>::NT, (XTma<N, SD, SP>::MIN_BLOCKS))
+    k_xleap_tma(Fields fp0, XArgs xa, const __grid_constant__ XMaps maps) {
+  using XT = XTma<N, SD, SP>;
+  const Fields fp = at_chain(fp0, blockIdx.y);
+  using C = Cfg<N>;
+  constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* s_ex = reinterpret_cast<float2*>(smem);          // W tile, then the transform's exchange
+  float2* s_d = s_ex + XT::TILE;                            // delta tile [row][column] (SD)
+  float2* s_p = s_d + (SD ? XT::TILE : 0);                  // p tile (SP)
+  __shared__ float2 s_tw[N];
+  __shared__ int s_thr[MAXB], s_mthr[MAXB];
+  __shared__ float s_il[MAXB], s_im[MAXB], s_ims[MAXB];
+  __shared__ __align__(8) uint64_t bar;
+  const int t = threadIdx.x;
+  DevState* ds = fp.ds;
+  const int id = tile_id<N>();
+  const Tile<N> T = tile_x<N>(id);
+  const bool staged = id < N * C::ZB;
+  const int cur = ds->cur;
+  const int sbuf = xa.first ? cur : 1 - cur;
+  if (staged && t == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    mbar_expect_tx(&bar, (uint32_t)XT::SMEM);
+    const int kz0 = T.kz0, ky = T.ky0, ch = blockIdx.y;
+    tma_load_4d(s_ex, &maps.W, kz0, ky, 0, ch, &bar);
+    if constexpr (SD) tma_load_4d(s_d, sbuf ? &maps.d1 : &maps.d0, kz0, ky, 0, ch, &bar);
+    if constexpr (SP) tma_load_4d(s_p, &maps.ph, kz0, ky, 0, ch, &bar);
+  }
+  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
+  for (int i = t; i < MAXB; i += NT) {
+    s_thr[i] = ds->thr[i];
+    s_mthr[i] = ds->mthr[i];
+    s_il[i] = ds->inv_lambda[i];
+    s_im[i] = ds->inv_M[i];
+    s_ims[i] = ds->inv_ms[i];
+  }
+  const float2* src = dsel(fp, sbuf);
+  if (!staged) {
+    for (int i = t; i < XT::TILE; i += NT) {
+      const int r = i / F, f = i % F;
+      const long long g = T.base + (long long)r * T.rs + (long long)f * T.cs;
+      s_ex[i] = fp.W[g];
+      if constexpr (SD) s_d[i] = src[g];
+      if constexpr (SP) s_p[i] = fp.ph[g];
+    }
+  }
+  __syncthreads();
+  if (staged) {
+    bool ok = mbar_wait(&bar, 0);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+      // record the timeout, then give the copies one more bounded wait so that
+      // none is left writing into this block's shared memory when it exits
+      if (t == 0) {
+        atomicOr(&ds->status, (int)ST_TIMEOUT);
+        mbar_wait(&bar, 0);
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  const int f = t % F;
+  const int ja = t / F;
+  const int ky = T.ky0 + f * T.dky, kz = T.kz0 + f * T.dkz;
+  const int ny = sgn_n<N>(ky);
+  const int n2yz = ny * ny + kz * kz;
+  const float wk = (kz == 0 || kz == C::H) ? 1.f : 2.f;
+  (void)wk;
+  const long long colo = T.base + (long long)f * T.cs;
+  const bool mm = fp.mass_mode != 0;
+  const float scb = bin_scale(fp.n_bins, N), scm = bin_scale(fp.n_mass, N);
+  float2 v[C::RMAX];
+  if (ja < R1) {
+#pragma unroll
+    for (int b = 0; b < R2; ++b) v[b] = s_ex[(ja + R1 * b) * F + f];
+  }
+  __syncthreads();   // the exchange below overwrites the W tile
+  fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
+  const int jc = t / F;
+  float2* dst = dsel(fp, 1 - cur);
+  const float eps = (float)ds->eps;
+  const float ek = xa.first ? 0.5f * eps : eps;
+  if (jc < R2) {
+#pragma unroll
+    for (int d = 0; d < R1; ++d) {
+      const int k = jc + R2 * d;
+      const int nx = sgn_n<N>(k);
+      const int n2 = nx * nx + n2yz;
+      const int m = bin_est(n2, s_thr, scb, fp.n_bins);
+      const long long gi = colo + (long long)k * T.rs;
+      float2 xx = SD ? s_d[k * F + f] : src[gi];
+      float2 pp = SP ? s_p[k * F + f] : fp.ph[gi];
+      if (m >= 0) {
+        const float il = s_il[m];
+        float im = s_im[m];
+        if (mm) im *= s_ims[bin_est(n2, s_mthr, scm, fp.n_mass)];
+        const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
+        pp.x = fmaf(-ek, gx, pp.x);
+        pp.y = fmaf(-ek, gy, pp.y);
+        const float sft = eps * im;
+        xx.x = fmaf(sft, pp.x, xx.x);
+        xx.y = fmaf(sft, pp.y, xx.y);
+      } else {
+        xx = make_float2(0.f, 0.f);
+        pp = make_float2(0.f, 0.f);
+      }
+      const long long idx = colo + (long long)k * T.rs;
+      fp.ph[idx] = pp;
+      dst[idx] = xx;
+      v[d] = xx;
+    }
+  }
+  fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+  if (ja < R1) {
+#pragma unroll
+    for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
   }
 }
 
@@ -1051,6 +1193,78 @@ static PassTable make_table() {
   T.z_mom = [](const Fields& f, double* mom, cudaStream_t s) { L::template z<Z_C2R>(f, ZArgs{f.W, nullptr, nullptr, nullptr, -1, 0, mom}, 1, s); };
   T.z_sums = [](const Fields& f, int region, int n, cudaStream_t s) { L::template z<Z_SUMS>(f, ZArgs{nullptr, nullptr, nullptr, nullptr, region, 0}, n, s); };
   return T;
+}
+
+// ---------------------------------------------------------------- TMA x pass: maps and launch
+template <int N, int SD, int SP>
+void launch_xleap_tma(const Fields& f, const XMaps& m, int first, int nch, cudaStream_t s) {
+  k_xleap_tma<N, SD, SP><<<dim3(Cfg<N>::TILES, nch), Cfg<N>::NT, XTma<N, SD, SP>::SMEM, s>>>(
+      f, XArgs{-1, nullptr, first, -1}, m);
+}
+
+template <int N, int SD, int SP>
+XLeapTma xleap_entry() {
+  if (cudaFuncSetAttribute(k_xleap_tma<N, SD, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)XTma<N, SD, SP>::SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return launch_xleap_tma<N, SD, SP>;
+}
+
+template <int N>
+XLeapTma xleap_variant(int which) {
+  switch (which) {
+    case 1: return xleap_entry<N, 1, 1>();   // W, delta and p staged (two blocks per SM)
+    case 2: return xleap_entry<N, 1, 0>();   // W and delta staged (three blocks per SM)
+    case 3: return xleap_entry<N, 0, 0>();   // W staged (three blocks per SM)
+    default: return nullptr;
+  }
+}
+
+XLeapTma xleap_tma(int N, int which) {
+  switch (N) {
+    case 8: return xleap_variant<8>(which);
+    case 16: return xleap_variant<16>(which);
+    case 32: return xleap_variant<32>(which);
+    case 64: return xleap_variant<64>(which);
+    case 96: return xleap_variant<96>(which);
+    case 128: return xleap_variant<128>(which);
+    case 256: return xleap_variant<256>(which);
+    default: return nullptr;
+  }
+}
+
+bool make_xmaps(const Fields& f, int N, int nch, XMaps* out) {
+  out->ok = false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
+  const int ZP = ((N / 2 + 1) + 1) / 2 * 2;
+  const int F = N / 2 < 16 ? N / 2 : 16;
+  const unsigned long long plane = (unsigned long long)N * N * ZP;
+  const unsigned long long cs = f.spec_stride > 0 ? (unsigned long long)f.spec_stride : plane;
+  const cuuint64_t dims[4] = {(cuuint64_t)ZP, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(nch > 0 ? nch : 1)};
+  const cuuint64_t strides[3] = {(cuuint64_t)ZP * 8, (cuuint64_t)N * ZP * 8, cs * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)F, 1, (cuuint32_t)N, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  float2* bufs[4] = {f.W, f.dh[0], f.dh[1], f.ph};
+  CUtensorMap* maps[4] = {&out->W, &out->d0, &out->d1, &out->ph};
+  for (int i = 0; i < 4; ++i) {
+    if (encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_INT64, 4, bufs[i], dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  out->ok = true;
+  return true;
 }
 
 bool pass_table(int N, PassTable* out) {

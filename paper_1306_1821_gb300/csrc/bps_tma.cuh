@@ -65,6 +65,19 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
+// tiled tensor copy global -> shared of one box of a 4D tensor map (coordinates
+// innermost first: x, y, z, w), completing on `bar`.  The map lives in the
+// kernel's parameter space (__grid_constant__); x times the element size must
+// be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
 enum { BUF_D0 = 0, BUF_D1 = 1, BUF_PH = 2, BUF_W = 3 };   // half-spectrum buffers
 
 }  // namespace bps

@@ -51,31 +51,84 @@ def random_problems(base, count, seed0, f_sky=(0.2, 0.6), p_scale=(0.5, 2.0), p_
     return out
 
 
+def radial_table(wl, n_r=2049):
+    """The workload's radial selection sampled at r_j = j (L/2) / (n_r - 1) (inputs recipe)."""
+    r = np.arange(n_r) * (wl.box / 2.0 / (n_r - 1))
+    if wl.radial == "linear":
+        f = np.maximum(0.0, 1.0 - r / (wl.box / 2.0))
+    else:
+        f = np.exp(-(r / wl.r0) ** 2)
+    return np.broadcast_to(f, (wl.n_sub, n_r)).copy()
+
+
+class DeviceMocks:
+    """Surveys of the `inputs` recipe (true field of the workload's spectrum, cap x
+    radial response, Poisson counts) made on the device by the library's mock
+    calls (bps_mock_*), through one single-chain context of the grid."""
+
+    def __init__(self, wl, stream=None):
+        import torch
+        self.wl = wl
+        N, box = wl.N, wl.box
+        self.s = bps.Sampler(N, box, wl.n_sub, wl.n_bins, stream=stream)
+        n2 = np.arange(3 * (N // 2) ** 2 + 1, dtype=np.float64)
+        self.P = inputs.true_spectrum(2.0 * np.pi * np.sqrt(n2) / box, N, box)
+        self.P[0] = 0.0
+        self.table = radial_table(wl)
+        self.torch = torch
+
+    def make(self, wl, seed):
+        """(counts int32, R float32, delta float32) device tensors of one survey."""
+        torch = self.torch
+        N = wl.N
+        d = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+        R = torch.empty((wl.n_sub, N, N, N), dtype=torch.float32, device="cuda")
+        c = torch.empty((wl.n_sub, N, N, N), dtype=torch.int32, device="cuda")
+        bps.bps_mock_field(self.s.ctx, seed, self.P, d)
+        bps.bps_mock_response(self.s.ctx, wl.f_sky, wl.extra.get("axis", (0.0, 0.0, 1.0)), self.table, R)
+        bps.bps_mock_counts(self.s.ctx, seed, d, R, wl.b, wl.nbar, 0, c)
+        return c, R, d
+
+    def close(self):
+        self.s.close()
+
+
 def features(P, W):
     return np.concatenate([np.log(P), np.log(np.maximum(W, 1e-30))])
 
 
 def measure(problems, n_mass, n_moves=200, burn_in=100, eps_max=None, n_leapfrog=None, seed=17, stream=None,
-            sampler_mass=None):
+            sampler_mass=None, device_mocks=False, chunk=None):
     """Features [count, 2 n_bins] and targets [count, n_mass] from a batch of
     chains (one per problem), with P held at each problem's spectrum.
     Targets: ln s_j = -ln(V_j Mbar_j), clamped to +-ln 16.  V_j is a property of
     the posterior, not of the mass the chains move with: `sampler_mass` (a
     Preconditioner) lets the chains move with a learned mass, whose faster
     mixing gives less biased variances of the slow modes from the same number
-    of moves (a second round of training on chains of the improved sampler)."""
+    of moves (a second round of training on chains of the improved sampler).
+    device_mocks: make the surveys on the device (bps_mock_*) instead of by the
+    host recipe; chunk: at most this many chains per batch context."""
     import torch
+    if chunk is not None and len(problems) > chunk:
+        parts = [measure(problems[i:i + chunk], n_mass, n_moves, burn_in, eps_max, n_leapfrog, seed + i, stream,
+                         sampler_mass, device_mocks) for i in range(0, len(problems), chunk)]
+        return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
     wl0 = problems[0].wl
+    mocks = DeviceMocks(wl0, stream) if device_mocks else None
     cfg = bps.make_config(wl0.n_bins, n_leapfrog=n_leapfrog or wl0.n_leapfrog, eps_max=eps_max or wl0.eps_max,
                           jump=0, fixed_bias_index=0, seed=seed)
     wls = [p.wl for p in problems]
     batch = bps.bps_create_batch([w.N for w in wls], [w.box for w in wls], [w.n_sub for w in wls], cfg, stream)
     try:
         for j, pr in enumerate(problems):
-            delta, counts, R = inputs.make_survey(pr.wl)
-            bps.bps_batch_set_chain(batch, j, torch.from_numpy(counts).cuda(), torch.from_numpy(R).cuda(),
-                                    torch.from_numpy(delta.astype(np.float32)).cuda(), pr.P, np.array(pr.wl.b),
-                                    np.array(pr.wl.nbar), 0)
+            if mocks is not None:
+                c, R, d = mocks.make(pr.wl, pr.wl.seed)
+            else:
+                delta, counts, Rh = inputs.make_survey(pr.wl)
+                c, R = torch.from_numpy(counts).cuda(), torch.from_numpy(Rh).cuda()
+                d = torch.from_numpy(delta.astype(np.float32)).cuda()
+            bps.bps_batch_set_chain(batch, j, c, R, d, pr.P, np.array(pr.wl.b), np.array(pr.wl.nbar), 0)
+            del c, R, d
         n = len(problems)
         W = bps.bps_window_power(batch, wl0.n_bins, n)
         if sampler_mass is not None:
@@ -86,6 +139,8 @@ def measure(problems, n_mass, n_moves=200, burn_in=100, eps_max=None, n_leapfrog
         slots = [bps.bps_batch_record_slot(batch, j) for j in range(n)]
     finally:
         bps.bps_destroy(batch)
+        if mocks is not None:
+            mocks.close()
     feats = np.stack([features(pr.P, W[s]) for pr, s in zip(problems, slots)])
     targ = np.clip(np.stack([-np.log(V[s] * Mb[s]) for s in slots]), -LOG_CLAMP, LOG_CLAMP)
     return feats, targ
