@@ -513,6 +513,15 @@ bps_status bps_selftest_wait(bps_ctx* ctx, uint64_t limit_ns);
  * size changes only the grouping of the likelihood-energy partial sums. */
 int bps_z_line_pairs(const bps_ctx* ctx);
 
+/* Implementation of the leapfrog x pass in use by ctx (the first group of a
+ * batch): 0 loads its tiles straight into registers; 1, 2, 3 stage them in
+ * shared memory with tensor copies (W, delta and p; W and delta; W only).  The
+ * four give bit-identical results.  Chosen when the context is created, like
+ * bps_z_line_pairs: the first context of a (GPU model, grid, number of chains)
+ * kind times the four and keeps the fastest, cached with the z-pass choice;
+ * BPS_XTMA = 0..3 forces one, BPS_AUTOTUNE=0 keeps 0. */
+int bps_x_pass_variant(const bps_ctx* ctx);
+
 void bps_destroy(bps_ctx* ctx);
 
 #ifdef __cplusplus

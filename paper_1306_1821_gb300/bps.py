@@ -56,6 +56,7 @@ _SIGS = {
     "bps_set_data_host_u16": ([_P, _P, _P], ctypes.c_int),
     "bps_stage_data_host_u16": ([_P, _P, _P], ctypes.c_int),
     "bps_z_line_pairs": ([_P], ctypes.c_int),
+    "bps_x_pass_variant": ([_P], ctypes.c_int),
     "bps_adapt_step_size": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D], ctypes.c_int),
     "bps_set_preconditioner": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
     "bps_mlp_export": ([_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),

@@ -775,6 +775,71 @@ bps_status choose_zgrad(bps_ctx* ctx) {
   return BPS_OK;
 }
 
+// The leapfrog x pass has four implementations with bit-identical results: the
+// direct-load pass and three with tensor-copy staged tiles (W, delta and p; W and
+// delta; W only).  Which is fastest depends on the GPU, the grid and the number
+// of chains sharing a launch, so the first context of a kind times them on its
+// own (still empty) buffers like the z-pass tiles above and caches the choice
+// ("... xleap" keys).  BPS_XTMA = 0..3 forces one; BPS_AUTOTUNE=0 keeps the
+// direct pass.
+bps_status choose_xleap(bps_ctx* ctx) {
+  ctx->xleap = nullptr;
+  int which = 0;
+  const char* xe = std::getenv("BPS_XTMA");
+  const char* ae = std::getenv("BPS_AUTOTUNE");
+  const bool tune = !xe && !(ae && std::atoi(ae) == 0);
+  if (xe) which = std::atoi(xe);
+  if (!xe && !tune) return BPS_OK;
+  if (!make_xmaps(fields(ctx), ctx->N, ctx->batch, &ctx->xmaps)) return BPS_OK;   // no tensor maps: direct
+  if (tune) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    const std::string key = std::string(prop.name) + " N=" + std::to_string(ctx->N) + " chains=" +
+                            std::to_string(ctx->batch) + " xleap";
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_loaded) tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && it->second >= 0 && it->second <= 3) {
+      which = it->second;
+    } else {
+      cudaStream_t s = ctx->stream;
+      const Fields f = fields(ctx);
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int c = 0; c < 4; ++c) {
+        XLeapTma fn = c ? xleap_tma(ctx->N, c) : nullptr;
+        if (c && !fn) continue;
+        auto run = [&] {
+          if (c) fn(f, ctx->xmaps, 0, ctx->batch, s);
+          else ctx->pt.x_leap(f, 0, ctx->batch, s);
+        };
+        for (int w = 0; w < 2; ++w) run();
+        CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 5; ++r) run();
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          which = c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      CK(cudaGetLastError());
+      g_tune[key] = which;
+      tune_save();
+    }
+  }
+  if (which > 0) ctx->xleap = xleap_tma(ctx->N, which);
+  return BPS_OK;
+}
+
 // ------------------------------------------------------------------ group construction
 bps_status check_config(const bps_config* cfg, int min_sub) {
   if (cfg->n_bins < 1 || cfg->n_bins > MAXB) return fail(nullptr, BPS_EINVAL, "n_bins must be in 1..64");
@@ -897,16 +962,11 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
     delete ctx;
     return fail(nullptr, BPS_ECUDA, msg);
   }
-  // the leapfrog x pass with its tiles staged by tensor copies (BPS_XTMA = 1, 2
-  // or 3: which tiles, see xleap_tma) where the driver offers the tensor-map
-  // encoder; by default the direct-load pass
-  {
-    const char* xe = std::getenv("BPS_XTMA");
-    const int which = xe ? std::atoi(xe) : 0;
-    if (which > 0) {
-      ctx->xleap = xleap_tma(grid_n, which);
-      if (ctx->xleap && !make_xmaps(fields(ctx), grid_n, B, &ctx->xmaps)) ctx->xleap = nullptr;
-    }
+  if (choose_xleap(ctx) != BPS_OK) {
+    std::string msg = "x-pass autotuning failed: " + ctx->err;
+    free_all(ctx);
+    delete ctx;
+    return fail(nullptr, BPS_ECUDA, msg);
   }
   if (choose_zgrad(ctx) != BPS_OK) {
     std::string msg = "tile autotuning failed: " + ctx->err;
@@ -1316,6 +1376,15 @@ uint64_t bps_kernel_launches(const bps_ctx* ctx) {
   uint64_t n = ctx->launches;
   for (const bps_ctx* g : ctx->groups) n += g->launches;
   return n;
+}
+
+int bps_x_pass_variant(const bps_ctx* ctx) {
+  if (!ctx) return -1;
+  const bps_ctx* g = ctx->is_batch ? (ctx->groups.empty() ? nullptr : ctx->groups[0]) : ctx;
+  if (!g || !g->xleap) return 0;
+  for (int c = 1; c <= 3; ++c)
+    if (xleap_tma(g->N, c) == g->xleap) return c;
+  return 0;
 }
 
 int bps_z_line_pairs(const bps_ctx* ctx) {

@@ -1101,6 +1101,94 @@ __global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, u
   }
 }
 
+// The same check, four consecutive voxels per thread (one 16-byte load of R,
+// one 8- or 16-byte load of the counts, vector stores): every upload path of a
+// survey (16-bit counts checked in place, 32-bit counts converted into the
+// slot) sums in this one order, so they give the same data constants bit for
+// bit.  A z line holds whole 4-voxel groups (N is a multiple of 4).  The line
+// support is a warp minimum and maximum when a warp's 128 voxels lie on one z
+// line (N a multiple of 128), else a pair of atomics per thread with data.
+template <typename CT>
+__global__ void __launch_bounds__(256) k_data4(const CT* __restrict__ cin, const float* __restrict__ rin,
+                                               uint16_t* cout, float* rout, long long nv, double* part, int stride,
+                                               int2* span, int n_grid) {
+  __shared__ double s_red[32];
+  float sR = 0.f, cR = 0.f, sB = 0.f, cB = 0.f;
+  unsigned int no = 0, bad = 0;
+  const long long n4 = nv / 4;
+  const int lane = threadIdx.x & 31;
+  const bool warp_line = n_grid % 128 == 0;
+  for (long long q = blockIdx.x * 256LL + threadIdx.x; q < n4; q += (long long)gridDim.x * 256) {
+    int c4[4];
+    if constexpr (sizeof(CT) == 2) {
+      const ushort4 cc = reinterpret_cast<const ushort4*>(cin)[q];
+      c4[0] = cc.x; c4[1] = cc.y; c4[2] = cc.z; c4[3] = cc.w;
+    } else {
+      const int4 cc = reinterpret_cast<const int4*>(cin)[q];
+      c4[0] = cc.x; c4[1] = cc.y; c4[2] = cc.z; c4[3] = cc.w;
+    }
+    const float4 rr = reinterpret_cast<const float4*>(rin)[q];
+    const float r4[4] = {rr.x, rr.y, rr.z, rr.w};
+    unsigned short o4[4];
+    float or4[4];
+    int first = -1, last = -1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float r = r4[j];
+      const int n = c4[j];
+      const bool rok = (r >= 0.f) && isfinite(r);
+      const bool nok = n >= 0 && n <= 65535;
+      if (!rok || !nok || (r == 0.f && n > 0)) ++bad;
+      o4[j] = (unsigned short)(nok ? n : 0);
+      or4[j] = rok ? r : 0.f;
+      if (rok && r > 0.f) {
+        if (first < 0) first = j;
+        last = j;
+        kahan_add(sR, cR, r);
+        const float fn = (float)(nok ? n : 0);
+        kahan_add(sB, cB, fn * fn / r);
+        ++no;
+      }
+    }
+    if (cout) reinterpret_cast<ushort4*>(cout)[q] = make_ushort4(o4[0], o4[1], o4[2], o4[3]);
+    if (rout) reinterpret_cast<float4*>(rout)[q] = make_float4(or4[0], or4[1], or4[2], or4[3]);
+    if (span) {
+      const int z0 = (int)((q * 4) % n_grid);
+      const int line = (int)((q * 4) / n_grid);
+      int lo = first >= 0 ? z0 + first : 0x7fffffff;
+      int hi = last >= 0 ? z0 + last + 1 : -1;
+      if (warp_line) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+          hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane != 0) hi = -1;
+      }
+      if (hi >= 0) {
+        atomicMax(&span[line].x, n_grid - (lo & ~3));
+        atomicMax(&span[line].y, (hi + 3) & ~3);
+      }
+    }
+  }
+  double v0 = block_sum<256>((double)sR - (double)cR, s_red);
+  double v1 = block_sum<256>((double)sB - (double)cB, s_red);
+  double v2 = block_sum<256>((double)no, s_red);
+  double v3 = block_sum<256>((double)bad, s_red);
+  if (threadIdx.x == 0) {
+    part[0 * stride + blockIdx.x] = v0;
+    part[1 * stride + blockIdx.x] = v1;
+    part[2 * stride + blockIdx.x] = v2;
+    part[3 * stride + blockIdx.x] = v3;
+  }
+}
+
+// the vectorised check applies to whole 4-voxel groups with aligned pointers
+inline bool data4_ok(const void* cin, size_t csz, const void* rin, const void* cout, const void* rout, long long nv) {
+  auto al = [](const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; };
+  return nv % 128 == 0 && al(cin, 4 * csz) && al(rin, 16) && al(cout, 8) && al(rout, 16);
+}
+
 __global__ void k_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
                                uint64_t* out) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -1285,11 +1373,17 @@ void launch_rebuild(const Fields& fp, long long nv, int region, int blocks, int 
 }
 void launch_data(const int32_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
                  int stride, int blocks, int2* span, int n_grid, cudaStream_t s) {
-  k_data<int32_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
+  if (data4_ok(cin, sizeof(int32_t), rin, cout, rout, nv))
+    k_data4<int32_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
+  else
+    k_data<int32_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
 }
 void launch_data16(const uint16_t* cin, const float* rin, uint16_t* cout, float* rout, long long nv, double* part,
                    int stride, int blocks, int2* span, int n_grid, cudaStream_t s) {
-  k_data<uint16_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
+  if (data4_ok(cin, sizeof(uint16_t), rin, cout, rout, nv))
+    k_data4<uint16_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
+  else
+    k_data<uint16_t><<<blocks, 256, 0, s>>>(cin, rin, cout, rout, nv, part, stride, span, n_grid);
 }
 void launch_philox_words(uint64_t seed, uint64_t it, uint64_t stage, uint64_t sub, uint64_t blk0, size_t n,
                          uint64_t* out, cudaStream_t s) {

@@ -344,6 +344,7 @@ def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
     code = ("from paper_1306_1821_gb300 import bps\n"
             "cfg = bps.make_config(2, n_leapfrog=2, eps_max=0.1)\n"
             "b = bps.bps_create_batch([8, 8, 8], [100.0] * 3, [1, 1, 1], cfg)\n"
+            "print(bps.load().bps_x_pass_variant(b))\n"
             "print(bps.bps_z_line_pairs(b))\n"
             "bps.bps_destroy(b)\n")
     env = dict(os.environ, BPS_TUNE_CACHE=str(path))
@@ -352,13 +353,18 @@ def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
                          timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     lp = int(out.stdout.strip().splitlines()[-1])
+    xv = int(out.stdout.strip().splitlines()[-2])
     assert lp in (4, 8, 16)
+    assert xv in (0, 1, 2, 3)
     cache = json.loads(path.read_text())
     assert any(k.endswith("N=8 chains=3 zpairs") and v == lp for k, v in cache.items())
+    # the x-pass implementation (four with bit-identical results) is tuned and cached too
+    assert any(k.endswith("N=8 chains=3 xleap") and v == xv for k, v in cache.items())
     monkeypatch.setenv("BPS_AUTOTUNE", "0")
     s = bps.Sampler(8, 100.0, 1, 2)
     try:
         assert bps.bps_z_line_pairs(s.ctx) == 8
+        assert bps.load().bps_x_pass_variant(s.ctx) == 0
     finally:
         s.close()
 

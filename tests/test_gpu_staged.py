@@ -37,10 +37,12 @@ def start_state(s, pb):
     bps.bps_set_spectrum(s.ctx, torch.from_numpy(pb.dh32).cuda())
 
 
-def test_staged_upload_gives_the_synchronous_chain(torch_cuda):
+@pytest.mark.parametrize("N", [32, 128])
+def test_staged_upload_gives_the_synchronous_chain(torch_cuda, N):
+    # 32^3: the data check widens each line's support per thread; 128^3: per warp
     from paper_1306_1821_gb300 import bps
     torch = torch_cuda
-    pb = Problem(32, n_sub=2, n_bins=4, n_leapfrog=4, eps_max=0.2)
+    pb = Problem(N, n_sub=2, n_bins=4, n_leapfrog=4, eps_max=0.2 if N == 32 else 0.05)
     ref = pb.gpu(seed=13, jump=1)
     st = fresh(pb, 13)
     try:
