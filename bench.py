@@ -362,8 +362,8 @@ def run_ours(args):
         bps.bps_gibbs_iterate(s.ctx, args.warmup)
 
     # ---- device-timed region: K Gibbs iterations, inputs resident in HBM.  Every
-    # PROFILE_EVERY-th iteration runs with per-stage event pairs (launched
-    # directly); the others replay the iteration's CUDA graph.
+    # PROFILE_EVERY-th iteration replays the iteration's graph with event-record
+    # nodes around the leapfrog kernels; the others replay the plain graph.
     bps.bps_profile_read(s.ctx)
     l0 = bps.bps_kernel_launches(s.ctx)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -497,8 +497,9 @@ def run_ours(args):
                                                    "GBps": bytes_kind[i] / (per_launch_ms[i] * 1e-3) / 1e9,
                                                    **(z_info if i == 2 else {})}
                                  for i in range(4)},
-            "profiled_iterations": f"1 in {PROFILE_EVERY} (event pairs around each leapfrog kernel, launched "
-                                   f"directly); the rest replay the iteration's CUDA graph",
+            "profiled_iterations": f"1 in {PROFILE_EVERY} replays a second CUDA graph of the iteration with "
+                                   f"event-record nodes around each leapfrog kernel; the rest replay the "
+                                   f"iteration's plain graph",
             "leapfrog_roofline": {"bytes": leap_bytes, "ms": leap_ms,
                                   "GBps": leap_bytes / (leap_ms * 1e-3) / 1e9,
                                   "frac": leap_bytes / (leap_ms * 1e-3) / 1e9 / peak},

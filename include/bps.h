@@ -467,7 +467,11 @@ uint64_t bps_kernel_launches(const bps_ctx* ctx);
 /* Per-kernel timing of the leapfrog passes of bps_hmc_step / bps_gibbs_iterate:
  * with enable = 1 the library records a CUDA event pair around every launch of
  * the four leapfrog kernels (0: x pass with kick/drift, 1: y inverse, 2: z pass
- * with the local force, 3: y forward) on the context's stream.
+ * with the local force, 3: y forward) on the context's stream.  In
+ * bps_gibbs_iterate a profiled iteration replays its own captured CUDA graph,
+ * the iteration with event-record nodes around those kernels, and the times are
+ * read after each replay (a host synchronisation per profiled iteration); the
+ * kernels run as in an unprofiled replay, without host launch gaps.
  * bps_profile_read synchronises the stream and returns, per kernel kind, the
  * summed device milliseconds ms[4] and the launch counts n[4] since the last
  * read (then resets them).  Timing only; results are unchanged. */

@@ -572,6 +572,10 @@ def bps_z_line_pairs(ctx):
     return int(load().bps_z_line_pairs(ctx))
 
 
+def bps_x_pass_variant(ctx):
+    return int(load().bps_x_pass_variant(ctx))
+
+
 def bps_version():
     return load().bps_version().decode()
 

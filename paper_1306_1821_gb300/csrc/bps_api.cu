@@ -101,6 +101,13 @@ struct bps_ctx {
   bool prof = false;
   std::vector<cudaEvent_t> ev[4];
   size_t ev_used[4] = {0, 0, 0, 0};
+  // the iteration captured with event-record nodes around the leapfrog
+  // kernels: profiled iterations replay it instead of launching one by one
+  cudaGraphExec_t prof_graph = nullptr;
+  bool prof_graph_jump = false;
+  uint64_t prof_graph_launches = 0;
+  size_t prof_graph_events[4] = {0, 0, 0, 0};
+  bool capturing = false;
   double prof_ms[4] = {0, 0, 0, 0};
   uint64_t prof_n[4] = {0, 0, 0, 0};
   // running posterior moments (bps_posterior_moments): per-voxel sums of delta
@@ -359,15 +366,24 @@ void prof_fold(bps_ctx* ctx) {
       if (cudaEventElapsedTime(&ms, ctx->ev[k][i], ctx->ev[k][i + 1]) == cudaSuccess) {
         ctx->prof_ms[k] += ms;
         ctx->prof_n[k] += 1;
+      } else {
+        cudaGetLastError();   // a pair without a time is left out
       }
     }
     ctx->ev_used[k] = 0;
   }
 }
 
-// record one event of kernel kind k (start or end); no-op unless profiling
+// record one event of kernel kind k (start or end); no-op unless profiling.
+// Under stream capture the record becomes an event-record node of the graph
+// (the events were created beforehand, see capture_iteration).
 void prof_mark(bps_ctx* ctx, int k) {
   if (!ctx->prof) return;
+  if (ctx->capturing) {
+    if (ctx->ev_used[k] < ctx->ev[k].size())
+      cudaEventRecordWithFlags(ctx->ev[k][ctx->ev_used[k]++], ctx->stream, cudaEventRecordExternal);
+    return;
+  }
   if (ctx->ev_used[k] >= PROF_CAP && ctx->ev_used[k] % 2 == 0) prof_fold(ctx);
   if (ctx->ev_used[k] == ctx->ev[k].size()) {
     cudaEvent_t e;
@@ -601,7 +617,9 @@ float2* state_buffer(bps_ctx* ctx, int ch, int cur) { return ctx->dh[cur] + (siz
 
 void drop_graph(bps_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->prof_graph) cudaGraphExecDestroy(c->prof_graph);
   c->graph = nullptr;
+  c->prof_graph = nullptr;
 }
 
 void free_streams(bps_ctx* c) {
@@ -1192,10 +1210,73 @@ bps_status get_state_chain(bps_ctx* ctx, int ch, float* delta_dev, double* P, do
   return BPS_OK;
 }
 
+// Captures one Gibbs iteration of every chain of the groups into *out (kernels
+// counted per replay in *launches).  With `prof` the captured iteration also
+// holds event-record nodes around the leapfrog kernels of top (one group).
+bps_status capture_iteration(bps_ctx* top, const std::vector<bps_ctx*>& groups, double* rec_dev, int rec_len,
+                             long long iter_stride, bool jump, bool prof, cudaGraphExec_t* out, uint64_t* launches) {
+  bps_ctx* ctx = top;
+  cudaStream_t s = top->stream;
+  // capture on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured); the graph is replayed on the caller's
+  if (!top->cap_stream) CK(cudaStreamCreateWithFlags(&top->cap_stream, cudaStreamNonBlocking));
+  if (prof) {
+    prof_fold(top);   // also synchronises
+    // event-record nodes need their events before capture: two per leapfrog
+    // step and kernel kind
+    const size_t need = 2 * (size_t)top->cfg.n_leapfrog;
+    for (int k = 0; k < 4; ++k)
+      while (top->ev[k].size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        top->ev[k].push_back(e);
+      }
+  } else {
+    CK(cudaStreamSynchronize(s));
+  }
+  std::vector<uint64_t> before;
+  for (bps_ctx* gr : groups) before.push_back(gr->launches);
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(top->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (bps_ctx* gr : groups) gr->stream = top->cap_stream;
+  top->capturing = prof;
+  bps_status st = BPS_OK;
+  for (bps_ctx* gr : groups) {
+    st = gibbs_once(gr, rec_dev, rec_len, iter_stride, jump);
+    if (st != BPS_OK) break;
+  }
+  top->capturing = false;
+  for (bps_ctx* gr : groups) gr->stream = s;
+  cudaError_t e = cudaStreamEndCapture(top->cap_stream, &g);
+  // the kernels were captured, not launched: count them per replay instead
+  uint64_t captured = 0;
+  for (size_t i = 0; i < groups.size(); ++i) {
+    captured += groups[i]->launches - before[i];
+    groups[i]->launches = before[i];
+  }
+  if (prof)
+    for (int k = 0; k < 4; ++k) {
+      top->prof_graph_events[k] = top->ev_used[k];
+      top->ev_used[k] = 0;
+    }
+  if (st != BPS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  CK(e);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  *launches = captured;
+  return BPS_OK;
+}
+
 // Run n_iter Gibbs iterations of every chain of the groups, recording into
 // `rec_dev` [n_iter][chains][rec_len].  Iterations replay one captured CUDA
 // graph (captured on first use, or again after a change that alters the
-// launches); with kernel timing on they are launched directly instead.
+// launches).  With kernel timing on, a single-chain context replays a second
+// graph that also records the leapfrog kernels' events, reading the timings
+// after every replay; a batch launches directly.
 bps_status run_iterations(bps_ctx* top, const std::vector<bps_ctx*>& groups, int n_iter, double* rec_dev,
                           int rec_len, int n_chains, bool jump) {
   bps_ctx* ctx = top;
@@ -1205,9 +1286,9 @@ bps_status run_iterations(bps_ctx* top, const std::vector<bps_ctx*>& groups, int
     LAUNCHED(g, 1);
   }
   const long long iter_stride = (long long)n_chains * rec_len;
-  bool use_graph = true;
-  for (bps_ctx* g : groups) use_graph = use_graph && !g->prof;
-  if (!use_graph) {
+  bool prof = false;
+  for (bps_ctx* g : groups) prof = prof || g->prof;
+  if (prof && groups.size() != 1) {
     for (int i = 0; i < n_iter; ++i)
       for (bps_ctx* g : groups) {
         bps_status st = gibbs_once(g, rec_dev, rec_len, iter_stride, jump);
@@ -1215,40 +1296,34 @@ bps_status run_iterations(bps_ctx* top, const std::vector<bps_ctx*>& groups, int
       }
     return BPS_OK;
   }
-  if (top->graph && top->graph_jump != jump) drop_graph(top);
+  if (prof) {
+    if (top->prof_graph && top->prof_graph_jump != jump) {
+      cudaGraphExecDestroy(top->prof_graph);
+      top->prof_graph = nullptr;
+    }
+    if (!top->prof_graph) {
+      bps_status st = capture_iteration(top, groups, rec_dev, rec_len, iter_stride, jump, true, &top->prof_graph,
+                                        &top->prof_graph_launches);
+      if (st != BPS_OK) return st;
+      top->prof_graph_jump = jump;
+    }
+    for (int i = 0; i < n_iter; ++i) {
+      CK(cudaGraphLaunch(top->prof_graph, s));
+      for (int k = 0; k < 4; ++k) top->ev_used[k] = top->prof_graph_events[k];
+      prof_fold(top);   // the replay re-records the same events: read them now
+    }
+    top->launches += (uint64_t)n_iter * top->prof_graph_launches;
+    return BPS_OK;
+  }
+  if (top->graph && top->graph_jump != jump) {
+    cudaGraphExecDestroy(top->graph);
+    top->graph = nullptr;
+  }
   if (!top->graph) {
-    // capture on a private stream (the caller's may be the legacy default
-    // stream, which cannot be captured); the graph is replayed on the caller's
-    if (!top->cap_stream) CK(cudaStreamCreateWithFlags(&top->cap_stream, cudaStreamNonBlocking));
-    CK(cudaStreamSynchronize(s));
-    std::vector<uint64_t> before;
-    for (bps_ctx* gr : groups) before.push_back(gr->launches);
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(top->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (bps_ctx* gr : groups) gr->stream = top->cap_stream;
-    bps_status st = BPS_OK;
-    for (bps_ctx* gr : groups) {
-      st = gibbs_once(gr, rec_dev, rec_len, iter_stride, jump);
-      if (st != BPS_OK) break;
-    }
-    for (bps_ctx* gr : groups) gr->stream = s;
-    cudaError_t e = cudaStreamEndCapture(top->cap_stream, &g);
-    // the kernels were captured, not launched: count them per replay instead
-    uint64_t captured = 0;
-    for (size_t i = 0; i < groups.size(); ++i) {
-      captured += groups[i]->launches - before[i];
-      groups[i]->launches = before[i];
-    }
-    if (st != BPS_OK) {
-      if (g) cudaGraphDestroy(g);
-      return st;
-    }
-    CK(e);
-    e = cudaGraphInstantiate(&top->graph, g, 0);
-    cudaGraphDestroy(g);
-    CK(e);
+    bps_status st =
+        capture_iteration(top, groups, rec_dev, rec_len, iter_stride, jump, false, &top->graph, &top->graph_launches);
+    if (st != BPS_OK) return st;
     top->graph_jump = jump;
-    top->graph_launches = captured;
   }
   for (int i = 0; i < n_iter; ++i) CK(cudaGraphLaunch(top->graph, s));
   top->launches += (uint64_t)n_iter * top->graph_launches;

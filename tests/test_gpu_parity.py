@@ -344,7 +344,7 @@ def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
     code = ("from paper_1306_1821_gb300 import bps\n"
             "cfg = bps.make_config(2, n_leapfrog=2, eps_max=0.1)\n"
             "b = bps.bps_create_batch([8, 8, 8], [100.0] * 3, [1, 1, 1], cfg)\n"
-            "print(bps.load().bps_x_pass_variant(b))\n"
+            "print(bps.bps_x_pass_variant(b))\n"
             "print(bps.bps_z_line_pairs(b))\n"
             "bps.bps_destroy(b)\n")
     env = dict(os.environ, BPS_TUNE_CACHE=str(path))
@@ -364,7 +364,7 @@ def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
     s = bps.Sampler(8, 100.0, 1, 2)
     try:
         assert bps.bps_z_line_pairs(s.ctx) == 8
-        assert bps.load().bps_x_pass_variant(s.ctx) == 0
+        assert bps.bps_x_pass_variant(s.ctx) == 0
     finally:
         s.close()
 
