@@ -511,6 +511,7 @@ def run_ours(args):
                                  "step's Gibbs iteration"},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
+            "tuning": {"z_line_pairs": bps.bps_z_line_pairs(s.ctx), "x_pass_variant": bps.bps_x_pass_variant(s.ctx)},
         }
         if pk is not None:
             line["pk_ess"] = pk
