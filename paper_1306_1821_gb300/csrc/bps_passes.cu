@@ -958,26 +958,36 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
     }
   }
 
-  // forward transform of the packed pair, then split into the two half spectra
+  // forward transform of the packed pair, then split into the two half spectra:
+  // G_a[k] = (Y[k] + conj Y[N-k]) / 2 and G_b[k] = -i (Y[k] - conj Y[N-k]) / 2,
+  // k <= N/2.  Thread (f, c) holds Y[c + R2 d], d < R1; Y[N - k] of its k =
+  // c + R2 d sits in the same pair's thread R2 - c as element R1 - 1 - d (c > 0)
+  // or in its own element (R1 - d) mod R1 (c = 0), so the split takes one
+  // register shuffle per element instead of a pass through shared memory.
   fft2<N, R1, R2, FWD, MAP_ROW, LP>(v, s_buf, s_tw, t);
   {
+    static_assert(R1 % 2 == 0, "the split below covers k <= N/2 for even R1");
+    constexpr unsigned MASK = NTZ >= 32 ? 0xffffffffu : ((1u << NTZ) - 1u);
     const int f = t / R2, c = t % R2;
-    if (f < LP) {
+    const int lane = t & 31;
+    const int src = lane - c + (R2 - c) % R2;
+    float2* dst = (MODE == Z_GRAD) ? fp.W : (MODE == Z_NOISE) ? fp.ph : za.dst;
+    float2* da = dst + (L0 + 2 * f) * ZP;
+    float2* db = da + ZP;
 #pragma unroll
-      for (int d = 0; d < R1; ++d) s_buf[f * N + c + R2 * d] = v[d];
+    for (int d = 0; d <= R1 / 2; ++d) {
+      const float2 snd = v[R1 - 1 - d];
+      float2 rcv;
+      rcv.x = __shfl_sync(MASK, snd.x, src);
+      rcv.y = __shfl_sync(MASK, snd.y, src);
+      const int k = c + R2 * d;
+      if (f < LP && k <= H) {
+        const float2 yk = v[d];
+        const float2 ym = cconj(c == 0 ? v[(R1 - d) % R1] : rcv);
+        da[k] = make_float2(0.5f * (yk.x + ym.x), 0.5f * (yk.y + ym.y));
+        db[k] = make_float2(0.5f * (yk.y - ym.y), -0.5f * (yk.x - ym.x));
+      }
     }
-  }
-  __syncthreads();
-  float2* dst = (MODE == Z_GRAD) ? fp.W : (MODE == Z_NOISE) ? fp.ph : za.dst;
-  for (int i = t; i < LINES * (H + 1); i += NTZ) {
-    const int l = i / (H + 1), k = i - l * (H + 1);
-    const int f = l >> 1;
-    const float2 yk = s_buf[f * N + k];
-    const float2 ym = cconj(s_buf[f * N + (k == 0 ? 0 : N - k)]);
-    float2 g;
-    if ((l & 1) == 0) g = make_float2(0.5f * (yk.x + ym.x), 0.5f * (yk.y + ym.y));
-    else g = make_float2(0.5f * (yk.y - ym.y), -0.5f * (yk.x - ym.x));
-    dst[(L0 + l) * ZP + k] = g;
   }
 }
 
