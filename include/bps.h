@@ -511,7 +511,9 @@ bps_status bps_selftest_wait(bps_ctx* ctx, uint64_t limit_ns);
 /* Line pairs per tile (4, 8 or 16) of the force z pass of ctx (the first
  * group of a batch).  Chosen when the context is created: the first context of
  * a (GPU model, grid, number of chains) kind times the three tile sizes on its
- * own buffers and keeps the fastest; the choice is cached for the process and
+ * own buffers, once transforming every line (a full-sky survey) and once with
+ * the line supports of a centred ball of radius 0.45 N, and keeps the smallest
+ * total; the choice is cached for the process and
  * in the JSON file named by BPS_TUNE_CACHE (default $HOME/.cache/bps_tune.json),
  * so that later contexts and runs reuse it.  BPS_AUTOTUNE=0 keeps 8.  The tile
  * size changes only the grouping of the likelihood-energy partial sums. */
