@@ -115,7 +115,10 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
   __shared__ int s_thr[MAXB], s_mthr[MAXB];
   __shared__ float s_il[MAXB], s_im[MAXB], s_sm[MAXB], s_ims[MAXB], s_sms[MAXB], s_js[MAXB];
   __shared__ double s_red[32];
-  __shared__ double s_wb[BINNED ? NW : 1][MAXB];
+  // per-warp bin sums as compensated FP32 pairs (sum, error): FP64 arithmetic is
+  // scarce on this GPU, and each pair keeps the sum of the FP32 terms it was given
+  // to about twice FP32 precision
+  __shared__ float s_wh[BINNED ? NW : 1][MAXB], s_wl[BINNED ? NW : 1][MAXB];
 
   const int t = threadIdx.x;
   DevState* ds = fp.ds;
@@ -136,7 +139,10 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
     s_sms[i] = ds->sqrt_ms[i];
     s_js[i] = ds->js[i];
     if constexpr (BINNED) {
-      for (int w = 0; w < NW; ++w) s_wb[w][i] = 0.0;
+      for (int w = 0; w < NW; ++w) {
+        s_wh[w][i] = 0.f;
+        s_wl[w][i] = 0.f;
+      }
     }
   }
   __syncthreads();
@@ -435,13 +441,14 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
     const int* thr = MASSBINS ? s_mthr : s_thr;
     const int nb = MASSBINS ? fp.n_mass : fp.n_bins;
     const float scl = MASSBINS ? scm : scb;
-    double* wb = s_wb[warp];
+    float* wh = s_wh[warp];
+    float* wl = s_wl[warp];
     for (int col = warp; col < F; col += NW) {
       const int nyc = sgn_n<N>(T.ky0 + col * T.dky), kzc = T.kz0 + col * T.dkz;
       const int n2c = nyc * nyc + kzc * kzc;
       const int a0 = lane * L, a1 = min(a0 + L, HN + 1);
       int mf = -1, ml = -1, mc = -1, nxt = 0x7fffffff;
-      float vf = 0.f, vl = 0.f, vc = 0.f;   // FP32 within the warp (FP64 is slow here); FP64 from the warp's bins on
+      float vf = 0.f, vl = 0.f, vc = 0.f;   // FP32 runs; the warp's bins are compensated FP32 pairs
       bool first_done = false;
       for (int a = a0; a < a1; ++a) {
         const int n2 = a * a + n2c;
@@ -462,7 +469,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
         if (m != mc) {
           if (mc >= 0) {                                  // close the current run
             if (!first_done) { mf = mc; vf = vc; first_done = true; }
-            else wb[mc] += (double)vc;                    // a run inside this lane only
+            else two_sum_add(wh[mc], wl[mc], vc);       // a run inside this lane only
           }
           mc = m;
           vc = 0.f;
@@ -492,15 +499,19 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
           if (lane + o < 32 && pm == mm2) vv += pv;
         }
         const int prev = __shfl_up_sync(0xffffffffu, mm2, 1);
-        if ((lane == 0 || prev != mm2) && mm2 >= 0) wb[mm2] += (double)vv;
+        if ((lane == 0 || prev != mm2) && mm2 >= 0) two_sum_add(wh[mm2], wl[mm2], vv);
         __syncwarp();
       }
     }
     __syncthreads();
     for (int m = t; m < MAXB; m += NT) {
-      double sum = 0.0;
+      TwoSumAcc acc;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) sum += s_wb[w][m];
+      for (int w = 0; w < NW; ++w) {
+        acc.add(s_wh[w][m]);
+        acc.add(s_wl[w][m]);
+      }
+      double sum = acc.value();
       if constexpr (MODE == X_JGRAD) sum *= (double)s_js[m];
       fp.part[xa.region + m * fp.part_stride + blockIdx.x] = sum;
     }

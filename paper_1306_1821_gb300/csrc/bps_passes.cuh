@@ -214,6 +214,14 @@ struct TwoSumAcc {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// The TwoSumAcc step on a pair (s, c) held elsewhere (e.g. in shared memory).
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float z = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+  s = t;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
