@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
   if constexpr (MODE == X_JINV) {
     if (ds->jreuse) return;       // W already holds this force stage's input (uniform)
   }
-  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
+  load_twiddles<N>(s_tw, fp.tw, t, NT);
   for (int i = t; i < MAXB; i += NT) {
     s_thr[i] = ds->thr[i];
     s_mthr[i] = ds->mthr[i];
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
 #pragma unroll
       for (int b = 0; b < R2; ++b) v[b] = in[colo + (long long)(ja + R1 * b) * T.rs];
     }
-    fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
+    fft2<N, R1, R2, FWD, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
   }
   const int jc = t / F;                       // row group of the Fourier (kx-) layout
   const bool act = jc < R2;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
         v[d] = xx;
       }
     }
-    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    fft2<N, R2, R1, INV, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
     if (ja < R1) {
 #pragma unroll
       for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
       }
       }
     }
-    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    fft2<N, R2, R1, INV, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
     if (ja < R1) {
 #pragma unroll
       for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
         }
       }
     }
-    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    fft2<N, R2, R1, INV, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
     float2* out = (MODE == X_INV && xa.dst) ? xa.dst : fp.W;   // no destination: this chain's W
     if (ja < R1) {
 #pragma unroll
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, (XTma<N, SD, SP>::MIN_BLOCKS))
     if constexpr (SD) tma_load_4d(s_d, sbuf ? &maps.d1 : &maps.d0, kz0, ky, 0, ch, &bar);
     if constexpr (SP) tma_load_4d(s_p, &maps.ph, kz0, ky, 0, ch, &bar);
   }
-  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
+  load_twiddles<N>(s_tw, fp.tw, t, NT);
   for (int i = t; i < MAXB; i += NT) {
     s_thr[i] = ds->thr[i];
     s_mthr[i] = ds->mthr[i];
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, (XTma<N, SD, SP>::MIN_BLOCKS))
     for (int b = 0; b < R2; ++b) v[b] = s_ex[(ja + R1 * b) * F + f];
   }
   __syncthreads();   // the exchange below overwrites the W tile
-  fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
+  fft2<N, R1, R2, FWD, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
   const int jc = t / F;
   float2* dst = dsel(fp, 1 - cur);
   const float eps = (float)ds->eps;
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, (XTma<N, SD, SP>::MIN_BLOCKS))
       v[d] = xx;
     }
   }
-  fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+  fft2<N, R2, R1, INV, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
   if (ja < R1) {
 #pragma unroll
     for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
@@ -686,16 +686,16 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_YPASS_MIN_BLOCKS) k_ypass(Fiel
       for (int d = 0; d < R1; ++d) v[d] = data[colo + (long long)(j + R2 * d) * T.rs];
     }
   }
-  for (int i = t; i < N; i += NT) s_tw[i] = fp.tw[i];
+  load_twiddles<N>(s_tw, fp.tw, t, NT);
   __syncthreads();
   if constexpr (DIR == FWD) {
-    fft2<N, R1, R2, FWD, MAP_COL, F>(v, s_ex, s_tw, t);
+    fft2<N, R1, R2, FWD, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
     if (j < R2) {
 #pragma unroll
       for (int d = 0; d < R1; ++d) data[colo + (long long)(j + R2 * d) * T.rs] = v[d];
     }
   } else {
-    fft2<N, R2, R1, INV, MAP_COL, F>(v, s_ex, s_tw, t);
+    fft2<N, R2, R1, INV, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
     if (j < R1) {
 #pragma unroll
       for (int b = 0; b < R2; ++b) data[colo + (long long)(j + R1 * b) * T.rs] = v[b];
@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       }
     }
   }
-  for (int i = t; i < N; i += NTZ) s_tw[i] = fp.tw[i];
+  load_twiddles<N>(s_tw, fp.tw, t, NTZ);
   float2 v[C::RMAX];
 
   if constexpr (STAGED) {
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       }
     }
     __syncthreads();
-    fft2<N, R2, R1, INV, MAP_ROW, LP>(v, s_buf, s_tw, t);
+    fft2<N, R2, R1, INV, MAP_ROW, LP, TwSquare<N>::value>(v, s_buf, s_tw, t);
   } else {
     float* sr = reinterpret_cast<float*>(s_buf);
     if constexpr (MODE == Z_NOISE) {
@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   // c + R2 d sits in the same pair's thread R2 - c as element R1 - 1 - d (c > 0)
   // or in its own element (R1 - d) mod R1 (c = 0), so the split takes one
   // register shuffle per element instead of a pass through shared memory.
-  fft2<N, R1, R2, FWD, MAP_ROW, LP>(v, s_buf, s_tw, t);
+  fft2<N, R1, R2, FWD, MAP_ROW, LP, TwSquare<N>::value>(v, s_buf, s_tw, t);
   {
     static_assert(R1 % 2 == 0, "the split below covers k <= N/2 for even R1");
     constexpr unsigned MASK = NTZ >= 32 ? 0xffffffffu : ((1u << NTZ) - 1u);

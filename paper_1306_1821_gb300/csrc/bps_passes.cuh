@@ -96,15 +96,19 @@ __device__ __forceinline__ int exidx(int f, int a, int c) {
 // In : thread (f, j<A) holds v[b] = x[j + A b], b < B.
 // Out: thread (f, j<B) holds v[d] = X[j + B d], d < A.
 // MAP_COL: f = t % F, j = t / F.   MAP_ROW: f = t / (A or B), j = t % (A or B).
-template <int N, int A, int B, int DIR, int MAP, int F>
+// tw: W_N^j at entry j, or (TW2, a square split A = B) W_N^(j c) at entry
+// c A + j, where the lanes j of one twiddle read hit consecutive entries instead
+// of entries c apart (load_twiddles).
+template <int N, int A, int B, int DIR, int MAP, int F, bool TW2 = false>
 __device__ __forceinline__ void fft2(float2* v, float2* ex, const float2* tw, int t) {
+  static_assert(!TW2 || A == B, "the two-dimensional twiddle table is for square splits");
   int f, j;
   if constexpr (MAP == MAP_COL) { f = t % F; j = t / F; } else { f = t / A; j = t % A; }
   if (j < A && f < F) {
     Dft<B, DIR>::run(v);
 #pragma unroll
     for (int c = 1; c < B; ++c) {
-      float2 w = tw[j * c];
+      float2 w = TW2 ? tw[c * A + j] : tw[j * c];
       if constexpr (DIR == INV) w.y = -w.y;
       v[c] = cmul(v[c], w);
     }
@@ -119,6 +123,18 @@ __device__ __forceinline__ void fft2(float2* v, float2* ex, const float2* tw, in
     Dft<A, DIR>::run(v);
   }
   __syncthreads();
+}
+
+// The shared-memory twiddle table of the field passes in the layout their fft2
+// calls read (TwSquare<N>: two-dimensional for a square split).
+template <int N>
+struct TwSquare {
+  static constexpr bool value = Cfg<N>::R1 == Cfg<N>::R2;
+};
+template <int N>
+__device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* tw, int t, int nt) {
+  constexpr int R = Cfg<N>::R1;
+  for (int i = t; i < N; i += nt) s_tw[i] = TwSquare<N>::value ? tw[(i / R) * (i % R)] : tw[i];
 }
 
 // ------------------------------------------------------------ tile geometry
