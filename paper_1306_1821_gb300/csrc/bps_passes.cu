@@ -227,8 +227,9 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
 #pragma unroll
       for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
     }
-    double sK = block_sum<NT>(eK.value(), s_red);
-    double sP = block_sum<NT>(eP.value(), s_red);
+    float* s_rf = reinterpret_cast<float*>(s_red);
+    double sK = block_sum2<NT>(eK, s_rf);
+    double sP = block_sum2<NT>(eP, s_rf);
     if (t == 0) {
       fp.part[xa.region + blockIdx.x] = sK;
       fp.part[xa.region + fp.part_stride + blockIdx.x] = sP;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
       for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
     }
     if constexpr (MODE == X_LEAPG) {
-      const double sG = block_sum<NT>((double)eG, s_red);
+      const double sG = block_sum2<NT>(pair_of(eG), reinterpret_cast<float*>(s_red));
       if (t == 0) fp.part[xa.region + blockIdx.x] = sG;
     }
     return;
@@ -324,9 +325,10 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
         }
       }
     }
-    double sK = block_sum<NT>(eK.value(), s_red);
-    double sP = block_sum<NT>(eP.value(), s_red);
-    double sG = block_sum<NT>((double)eG, s_red);
+    float* s_rf = reinterpret_cast<float*>(s_red);
+    double sK = block_sum2<NT>(eK, s_rf);
+    double sP = block_sum2<NT>(eP, s_rf);
+    double sG = block_sum2<NT>(pair_of(eG), s_rf);
     if (t == 0) {
       fp.part[xa.region + blockIdx.x] = sK;
       fp.part[xa.region + fp.part_stride + blockIdx.x] = sP;
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
         xa.dst[colo + (long long)k * T.rs] = g;
       }
     }
-    double sP = block_sum<NT>(eP.value(), s_red);
+    double sP = block_sum2<NT>(eP, reinterpret_cast<float*>(s_red));
     if (t == 0) fp.part[xa.region + blockIdx.x] = sP;
     return;
   }
@@ -899,10 +901,11 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       const int nsub = ds->nsub;
       const int loa = f < LP ? s_lo[2 * f] : 0, hia = f < LP ? s_hi[2 * f] : 0;
       const int lob = f < LP ? s_lo[2 * f + 1] : 0, hib = f < LP ? s_hi[2 * f + 1] : 0;
-      // per-warp FP64 sums of all 3 nsub quantities, then one pass over the warps
-      // (the same additions, in the same order, as one block sum per quantity)
+      // per-warp sums of all 3 nsub quantities as compensated FP32 pairs, then one
+      // pass over the warps (the same additions, in the same order, as one block
+      // sum per quantity)
       constexpr int NW = (NTZ + 31) / 32;
-      __shared__ double s_ws[NW][3 * MAXS];
+      __shared__ float s_ws[NW][3 * MAXS][2];   // compensated pairs
       const int lane = t & 31, w = t >> 5;
       for (int l = 0; l < nsub; ++l) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
@@ -921,19 +924,28 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
             s3 += ra * da * da + rb * db * db;
           }
         }
-        const double t1 = warp_sum((double)s1), t2 = warp_sum((double)s2), t3 = warp_sum((double)s3);
+        float c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        warp_sum2<NTZ>(s1, c1);
+        warp_sum2<NTZ>(s2, c2);
+        warp_sum2<NTZ>(s3, c3);
         if (lane == 0) {
-          s_ws[w][3 * l + 0] = t1;
-          s_ws[w][3 * l + 1] = t2;
-          s_ws[w][3 * l + 2] = t3;
+          s_ws[w][3 * l + 0][0] = s1;
+          s_ws[w][3 * l + 0][1] = c1;
+          s_ws[w][3 * l + 1][0] = s2;
+          s_ws[w][3 * l + 1][1] = c2;
+          s_ws[w][3 * l + 2][0] = s3;
+          s_ws[w][3 * l + 2][1] = c3;
         }
       }
       __syncthreads();
       for (int q = t; q < 3 * nsub; q += NTZ) {
-        double r = 0.0;
+        TwoSumAcc r;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) r += s_ws[i][q];
-        fp.part[za.region + q * fp.part_stride + blockIdx.x] = r;
+        for (int i = 0; i < NW; ++i) {
+          r.add(s_ws[i][q][0]);
+          r.add(s_ws[i][q][1]);
+        }
+        fp.part[za.region + q * fp.part_stride + blockIdx.x] = r.value();
       }
       return;
     }
@@ -964,7 +976,10 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
       }
     }
     if (want_e) {
-      double s = block_sum<NTZ>(0.5 * e.value(), s_red);
+      TwoSumAcc h;                 // halving is exact
+      h.s = 0.5f * e.s;
+      h.c = 0.5f * e.c;
+      double s = block_sum2<NTZ>(h, reinterpret_cast<float*>(s_red));
       if (t == 0) fp.part[za.region + blockIdx.x] = s;
     }
   }
@@ -1062,7 +1077,10 @@ __global__ void __launch_bounds__(256) k_rebuild(Fields fp0, long long nv, int r
     for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256)
       kahan_add(acc, comp, group(i));
   }
-  double s = block_sum<256>((double)acc - (double)comp, s_red);
+  TwoSumAcc k;                    // the Kahan sum acc - comp as a pair
+  k.s = acc;
+  k.c = -comp;
+  double s = block_sum2<256>(k, reinterpret_cast<float*>(s_red));
   if (threadIdx.x == 0) fp.part[region + blockIdx.x] = s;
 }
 

@@ -260,6 +260,60 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// Sum of the compensated pairs (s, c) of the lanes of this warp that exist in a
+// block of NT threads, by TwoSum steps in FP32 only: the total pair is in lane 0.
+// FP64 arithmetic is scarce on this GPU; a pair carries the sum to about twice
+// FP32 precision.  Shuffles name only the lanes that exist (a block need not
+// fill its last warp), and a lane adds only values from lanes that exist.
+template <int NT>
+__device__ __forceinline__ void warp_sum2(float& s, float& c) {
+  const int lane = threadIdx.x & 31;
+  const int nl = NT % 32 == 0 ? 32 : min(32, NT - (int)(threadIdx.x & ~31u));
+  const unsigned mask = nl >= 32 ? 0xffffffffu : ((1u << nl) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(mask, s, o), c2 = __shfl_down_sync(mask, c, o);
+    if (lane + o < nl) {
+      const float t = __fadd_rn(s, s2);
+      const float z = __fsub_rn(t, s);
+      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+      s = t;
+      c = __fadd_rn(c, __fadd_rn(c2, err));
+    }
+  }
+}
+
+// Deterministic block sum of per-thread compensated pairs; the FP64 result is
+// valid in thread 0 (one conversion there).  sh: >= 2 * ceil(NT / 32) floats.
+template <int NT>
+__device__ __forceinline__ double block_sum2(TwoSumAcc a, float* sh) {
+  float s = a.s, c = a.c;
+  warp_sum2<NT>(s, c);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    sh[2 * w] = s;
+    sh[2 * w + 1] = c;
+  }
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    TwoSumAcc t;
+#pragma unroll
+    for (int i = 0; i < (NT + 31) / 32; ++i) {
+      t.add(sh[2 * i]);
+      t.add(sh[2 * i + 1]);
+    }
+    r = t.value();
+  }
+  return r;
+}
+__device__ __forceinline__ TwoSumAcc pair_of(float x) {
+  TwoSumAcc a;
+  a.s = x;
+  return a;
+}
+
 // Per-bin accumulation for one element per thread of a column tile: within
 // each group of G consecutive lanes (one tile row) the bin is monotone along
 // the lanes, so lanes of one bin are contiguous; a segmented shuffle sum gives
