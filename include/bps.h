@@ -521,11 +521,13 @@ int bps_z_line_pairs(const bps_ctx* ctx);
 
 /* Implementation of the leapfrog x pass in use by ctx (the first group of a
  * batch): 0 loads its tiles straight into registers; 1, 2, 3 stage them in
- * shared memory with tensor copies (W, delta and p; W and delta; W only).  The
- * four give bit-identical results.  Chosen when the context is created, like
- * bps_z_line_pairs: the first context of a (GPU model, grid, number of chains)
- * kind times the four and keeps the fastest, cached with the z-pass choice;
- * BPS_XTMA = 0..3 forces one, BPS_AUTOTUNE=0 keeps 0. */
+ * shared memory with tensor copies (W, delta and p; W and delta; W only); 4
+ * streams the delta and p rows through a two-slot ring of quarter tiles filled
+ * by tensor copies while W is transformed.  The five give bit-identical
+ * results.  Chosen when the context is created, like bps_z_line_pairs: the
+ * first context of a (GPU model, grid, number of chains) kind times the five
+ * and keeps the fastest, cached with the z-pass choice; BPS_XTMA = 0..4 forces
+ * one, BPS_AUTOTUNE=0 keeps 0. */
 int bps_x_pass_variant(const bps_ctx* ctx);
 
 void bps_destroy(bps_ctx* ctx);

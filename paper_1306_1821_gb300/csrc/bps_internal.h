@@ -52,14 +52,16 @@ bool pass_table(int N, PassTable* out);
 // elements) for the TMA-staged leapfrog x pass; box 16 (or F) columns x 1 x N
 // rows x 1 chain.  ok = false when the driver offers no tensor-map encoder.
 struct XMaps {
-  CUtensorMap W, d0, d1, ph;
+  CUtensorMap W, d0, d1, ph;   // boxes of a whole tile (F columns x N rows)
+  CUtensorMap d0q, d1q, phq;   // boxes of a quarter tile (F columns x N/4 rows)
   bool ok = false;
 };
 bool make_xmaps(const Fields& f, int N, int nch, XMaps* out);
 // the leapfrog x pass with its tiles staged by tensor copies (first: the first
 // kick of a trajectory); nullptr where a grid has none
 using XLeapTma = void (*)(const Fields&, const XMaps&, int first, int nch, cudaStream_t);
-// which: 1 stages W, delta and p; 2 W and delta; 3 W only (0 or other: none)
+// which: 1 stages W, delta and p; 2 W and delta; 3 W only; 4 streams delta and p
+// through a ring of quarter tiles (0 or other: none)
 XLeapTma xleap_tma(int N, int which);
 
 // The fused y^-1 / z / y stage of a force evaluation (bps_yz.cu): one CTA per

@@ -662,6 +662,163 @@ __global__ void __launch_bounds__(Cfg<N>::NT, (XTma<N, SD, SP>::MIN_BLOCKS))
   }
 }
 
+// ------------------------------------------------------------------ x pass with a ring of quarters
+// The leapfrog x pass (X_LEAP) with the delta and p rows it reads after the
+// transform of W streamed through shared memory a quarter of the column at a
+// time: the kick and drift work through the column in quarters (rows
+// [q N/4, (q+1) N/4), the R1/4 elements of every thread), and a two-slot ring
+// holds the delta and p rows of two quarters.  One thread issues the tensor
+// copies of quarters 0 and 1 before W is loaded and transformed, and refills a
+// slot with quarter q+2 as soon as every thread has read quarter q, so the
+// kick reads shared memory while the next copies are in flight.  W is loaded
+// straight into registers as in the direct pass; a Nyquist tile (one element
+// per row, below the 16-byte copy width) reads delta and p directly.  32 KB of
+// ring per block keeps three blocks per SM.  Every wait is bounded; a block
+// whose copies do not arrive records the timeout, waits (bounded) for its
+// copies in flight and returns.
+template <int N>
+struct XRing {
+  using C = Cfg<N>;
+  static constexpr int QR = N / 4;                          // rows of one quarter
+  static constexpr int QT = QR * C::F;                      // complex elements of one quarter of one array
+  // a tensor copy lands on a 128-byte boundary: each quarter array starts at a
+  // multiple of QTP elements (QT rounded up to 128 bytes; 8^3 quarters are 64 bytes)
+  static constexpr int QTP = (QT * (int)sizeof(float2) + 127) / 128 * 128 / (int)sizeof(float2);
+  static constexpr uint32_t SLOT_BYTES = 2u * QT * sizeof(float2);   // bytes copied per slot (delta and p)
+  static constexpr size_t SMEM = 4 * (size_t)QTP * sizeof(float2);
+  static_assert(C::R1 % 4 == 0, "quarters of the column");
+  static_assert(QTP * sizeof(float2) % 128 == 0, "copy destinations on 128-byte boundaries");
+};
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
+    k_xleap_ring(Fields fp0, XArgs xa, const __grid_constant__ XMaps maps) {
+  using XR = XRing<N>;
+  const Fields fp = at_chain(fp0, blockIdx.y);
+  using C = Cfg<N>;
+  constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT, HQ = R1 / 4;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* s_ring = reinterpret_cast<float2*>(smem);         // [slot][delta, p][QR rows][F], arrays QTP apart
+  __shared__ float2 s_tw[N];
+  __shared__ __align__(16) float2 s_ex[N * F];
+  __shared__ int s_thr[MAXB], s_mthr[MAXB];
+  __shared__ float s_il[MAXB], s_im[MAXB], s_ims[MAXB];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int t = threadIdx.x;
+  DevState* ds = fp.ds;
+  const int id = tile_id<N>();
+  const Tile<N> T = tile_x<N>(id);
+  const bool staged = id < N * C::ZB;
+  const int cur = ds->cur;
+  const int sbuf = xa.first ? cur : 1 - cur;
+  const CUtensorMap* dmap = sbuf ? &maps.d1q : &maps.d0q;
+  auto issue = [&](int q) {                                 // thread 0: quarter q into slot q & 1
+    uint64_t* b = &bar[q & 1];
+    float2* slot = s_ring + (size_t)(q & 1) * 2 * XR::QTP;
+    mbar_expect_tx(b, XR::SLOT_BYTES);
+    tma_load_4d(slot, dmap, T.kz0, T.ky0, q * XR::QR, blockIdx.y, b);
+    tma_load_4d(slot + XR::QTP, &maps.phq, T.kz0, T.ky0, q * XR::QR, blockIdx.y, b);
+  };
+  if (staged && t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+    issue(0);
+    issue(1);
+  }
+  load_twiddles<N>(s_tw, fp.tw, t, NT);
+  for (int i = t; i < MAXB; i += NT) {
+    s_thr[i] = ds->thr[i];
+    s_mthr[i] = ds->mthr[i];
+    s_il[i] = ds->inv_lambda[i];
+    s_im[i] = ds->inv_M[i];
+    s_ims[i] = ds->inv_ms[i];
+  }
+  __syncthreads();   // the transform reads the twiddles before its first barrier
+  const int f = t % F;
+  const int ja = t / F;
+  const int ky = T.ky0 + f * T.dky, kz = T.kz0 + f * T.dkz;
+  const int ny = sgn_n<N>(ky);
+  const int n2yz = ny * ny + kz * kz;
+  const long long colo = T.base + (long long)f * T.cs;
+  const bool mm = fp.mass_mode != 0;
+  const float scb = bin_scale(fp.n_bins, N), scm = bin_scale(fp.n_mass, N);
+  const float2* src = dsel(fp, sbuf);
+  float2* dst = dsel(fp, 1 - cur);
+  float2 v[C::RMAX];
+  if (ja < R1) {
+#pragma unroll
+    for (int b = 0; b < R2; ++b) v[b] = fp.W[colo + (long long)(ja + R1 * b) * T.rs];
+  }
+  fft2<N, R1, R2, FWD, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
+  const int jc = t / F;
+  const bool act = jc < R2;
+  const float eps = (float)ds->eps;
+  const float ek = xa.first ? 0.5f * eps : eps;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2* slot = s_ring + (size_t)(q & 1) * 2 * XR::QTP;
+    if (staged) {
+      bool ok = mbar_wait(&bar[q & 1], (uint32_t)(q >> 1));
+      ok = __syncthreads_and(ok);
+      if (!ok) {
+        // record the timeout, then give the copies in flight one more bounded
+        // wait so that none is left writing into this block's shared memory
+        if (t == 0) {
+          atomicOr(&ds->status, (int)ST_TIMEOUT);
+          mbar_wait(&bar[q & 1], (uint32_t)(q >> 1));
+          if (q + 1 < 4) mbar_wait(&bar[(q + 1) & 1], (uint32_t)((q + 1) >> 1));
+        }
+        __syncthreads();
+        return;
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int e = 0; e < HQ; ++e) {
+        const int d = q * HQ + e;
+        const int k = jc + R2 * d;
+        const long long idx = colo + (long long)k * T.rs;
+        const int r = jc + R2 * e;                          // row within the quarter
+        float2 xx = staged ? slot[r * F + f] : src[idx];
+        float2 pp = staged ? slot[XR::QTP + r * F + f] : fp.ph[idx];
+        const int nx = sgn_n<N>(k);
+        const int n2 = nx * nx + n2yz;
+        const int m = bin_est(n2, s_thr, scb, fp.n_bins);
+        if (m >= 0) {
+          const float il = s_il[m];
+          float im = s_im[m];
+          if (mm) im *= s_ims[bin_est(n2, s_mthr, scm, fp.n_mass)];
+          const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
+          pp.x = fmaf(-ek, gx, pp.x);
+          pp.y = fmaf(-ek, gy, pp.y);
+          const float sft = eps * im;
+          xx.x = fmaf(sft, pp.x, xx.x);
+          xx.y = fmaf(sft, pp.y, xx.y);
+        } else {
+          xx = make_float2(0.f, 0.f);
+          pp = make_float2(0.f, 0.f);
+        }
+        fp.ph[idx] = pp;
+        dst[idx] = xx;
+        v[d] = xx;
+      }
+    }
+    if (staged && q + 2 < 4) {
+      __syncthreads();                                      // every thread has read this slot
+      if (t == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(q + 2);
+      }
+    }
+  }
+  fft2<N, R2, R1, INV, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
+  if (ja < R1) {
+#pragma unroll
+    for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
+  }
+}
+
 // ------------------------------------------------------------------ y pass
 template <int N, int DIR>
 __global__ void __launch_bounds__(Cfg<N>::NT, BPS_YPASS_MIN_BLOCKS) k_ypass(Fields fp0, int buf) {
@@ -1340,11 +1497,27 @@ XLeapTma xleap_entry() {
 }
 
 template <int N>
+void launch_xleap_ring(const Fields& f, const XMaps& m, int first, int nch, cudaStream_t s) {
+  k_xleap_ring<N><<<dim3(Cfg<N>::TILES, nch), Cfg<N>::NT, XRing<N>::SMEM, s>>>(f, XArgs{-1, nullptr, first, -1}, m);
+}
+
+template <int N>
+XLeapTma xleap_ring_entry() {
+  if (cudaFuncSetAttribute(k_xleap_ring<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XRing<N>::SMEM) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return launch_xleap_ring<N>;
+}
+
+template <int N>
 XLeapTma xleap_variant(int which) {
   switch (which) {
     case 1: return xleap_entry<N, 1, 1>();   // W, delta and p staged (two blocks per SM)
     case 2: return xleap_entry<N, 1, 0>();   // W and delta staged (three blocks per SM)
     case 3: return xleap_entry<N, 0, 0>();   // W staged (three blocks per SM)
+    case 4: return xleap_ring_entry<N>();    // delta and p through a ring of quarters (three blocks per SM)
     default: return nullptr;
   }
 }
@@ -1381,11 +1554,12 @@ bool make_xmaps(const Fields& f, int N, int nch, XMaps* out) {
   const cuuint64_t dims[4] = {(cuuint64_t)ZP, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(nch > 0 ? nch : 1)};
   const cuuint64_t strides[3] = {(cuuint64_t)ZP * 8, (cuuint64_t)N * ZP * 8, cs * 8};
   const cuuint32_t box[4] = {(cuuint32_t)F, 1, (cuuint32_t)N, 1};
+  const cuuint32_t boxq[4] = {(cuuint32_t)F, 1, (cuuint32_t)(N / 4), 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  float2* bufs[4] = {f.W, f.dh[0], f.dh[1], f.ph};
-  CUtensorMap* maps[4] = {&out->W, &out->d0, &out->d1, &out->ph};
-  for (int i = 0; i < 4; ++i) {
-    if (encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_INT64, 4, bufs[i], dims, strides, box, estr,
+  float2* bufs[7] = {f.W, f.dh[0], f.dh[1], f.ph, f.dh[0], f.dh[1], f.ph};
+  CUtensorMap* maps[7] = {&out->W, &out->d0, &out->d1, &out->ph, &out->d0q, &out->d1q, &out->phq};
+  for (int i = 0; i < 7; ++i) {
+    if (encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_INT64, 4, bufs[i], dims, strides, i < 4 ? box : boxq, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
