@@ -517,7 +517,9 @@ bps_status jump_gradient(bps_ctx* ctx, int kind) {
   const PassTable& P = ctx->pt;
   const int B = ctx->batch;
   P.x_jinv(f, B, s);
-  bps_status sf = force_stage(ctx, f, region_offset(ctx, RG_JLIK), false, s);
+  // the likelihood energy enters only the Hamiltonian at the two ends of the
+  // trajectory: a middle step's force stage skips its energy sums
+  bps_status sf = force_stage(ctx, f, kind == J_MID ? -1 : region_offset(ctx, RG_JLIK), false, s);
   if (sf != BPS_OK) return sf;
   P.x_jgrad(f, region_offset(ctx, RG_JGRAD), B, s);
   launch_jump_step(sa, region_offset(ctx, RG_JGRAD), P.x_tiles, region_offset(ctx, RG_JLIK),

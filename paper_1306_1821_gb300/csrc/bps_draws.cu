@@ -424,8 +424,9 @@ __device__ void jump_update(const ScalarArgs& a, int kind, double* sh) {
 
 // One leapfrog step of the jump after its gradient evaluation, in one launch:
 // blocks m < n_bins reduce the gradient d psi_J / d theta_m = (alpha - 1) +
-// (1/2N^3) sum_{k in m} w Re(conj(g) delta), block n_bins the likelihood energy
-// at theta; the last block to finish (a counter in the chain state, which it
+// (1/2N^3) sum_{k in m} w Re(conj(g) delta), block n_bins (launched for J_FIRST
+// and J_LAST only, whose update needs the energy) the likelihood energy at
+// theta; the last block to finish (a counter in the chain state, which it
 // resets) then applies the update of `kind`.
 __global__ void k_jump_step(ScalarArgs a0, int r_grad, int nx, int r_lik, int r_lik_move, int nz, int kind) {
   const ScalarArgs a = chain_args(a0, blockIdx.y);
@@ -443,7 +444,7 @@ __global__ void k_jump_step(ScalarArgs a0, int r_grad, int nx, int r_lik, int r_
   }
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(&ds->jdone, 1) == a.n_bins;
+    s_last = atomicAdd(&ds->jdone, 1) == (int)gridDim.x - 1;
   }
   __syncthreads();
   if (!s_last) return;
@@ -521,7 +522,8 @@ void launch_jump_begin(const ScalarArgs& a, int reuse, int nch, cudaStream_t s) 
 }
 void launch_jump_step(const ScalarArgs& a, int r_grad, int nx, int r_lik, int r_lik_move, int nz, int kind,
                       int nch, cudaStream_t s) {
-  k_jump_step<<<dim3(a.n_bins + 1, nch), 256, 0, s>>>(a, r_grad, nx, r_lik, r_lik_move, nz, kind);
+  k_jump_step<<<dim3(a.n_bins + (kind == J_MID ? 0 : 1), nch), 256, 0, s>>>(a, r_grad, nx, r_lik, r_lik_move, nz,
+                                                                          kind);
 }
 void launch_reduce_to(const ScalarArgs& a, int region, int nblk, int count, double scale, double* out_dev,
                       cudaStream_t s) {
