@@ -870,6 +870,41 @@ def run_schechter(args):
     return 0
 
 
+def run_bare(args):
+    """The 256^3 survey chain alone, for profiler captures of a small case: the
+    same survey, state and seeds as the timed leg, set up through the C ABI,
+    then --warmup and --steps Gibbs iterations; no other buffers, no timing and
+    no JSON line (about 2 GB on the device)."""
+    import numpy as np
+    import torch
+
+    from paper_1306_1821_gb300 import bps, inputs
+    if not os.path.exists(bps.LIB_PATH):
+        from paper_1306_1821_gb300 import build as b
+        b.build()
+    bps.load()
+    wl = inputs.WORKLOADS[WORKLOAD]
+    delta, counts, R = inputs.make_survey(wl, seed=wl.seed)
+    P0, b0, nbar0 = inputs.initial_state(wl)
+    s = bps.Sampler(wl.N, wl.box, wl.n_sub, wl.n_bins, n_leapfrog=wl.n_leapfrog, eps_max=wl.eps_max, jump=1,
+                    jump_leapfrog=wl.jump_leapfrog, jump_eps_max=wl.jump_eps_max, fixed_bias_index=wl.fixed_bias,
+                    seed=1)
+    try:
+        cnt = torch.from_numpy(counts).cuda()
+        Rd = torch.from_numpy(R).cuda()
+        bps.bps_set_data(s.ctx, cnt, Rd)
+        bps.bps_set_state(s.ctx, torch.from_numpy(delta.astype(np.float32)).cuda(), P0, b0, nbar0, 0)
+        del cnt, Rd
+        torch.cuda.empty_cache()
+        if args.warmup > 0:
+            bps.bps_gibbs_iterate(s.ctx, args.warmup)
+        rec = bps.bps_gibbs_iterate(s.ctx, args.steps, s.rec_len)
+        print(f"bare: {args.steps} Gibbs iterations of {wl.name}, HMC acceptance {float(np.mean(rec[:, -1])):.2f}")
+    finally:
+        s.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -886,7 +921,11 @@ def main(argv=None):
     ap.add_argument("--ess-iters", type=int, default=None,
                     help="Gibbs iterations of the P(k) ESS run (default 4000 at 256^3, 20000 per arm of precond128; "
                          "0 skips it)")
+    ap.add_argument("--bare", action="store_true",
+                    help="only the 256^3 chain: --warmup then --steps Gibbs iterations, no timing (profiler captures)")
     args = ap.parse_args(argv)
+    if args.bare:
+        return run_bare(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
