@@ -759,7 +759,11 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
   for (int q = 0; q < 4; ++q) {
     const float2* slot = s_ring + (size_t)(q & 1) * 2 * XR::QTP;
     if (staged) {
-      bool ok = mbar_wait(&bar[q & 1], (uint32_t)(q >> 1));
+      // one thread polls the barrier (256 pollers flood the shared-memory
+      // pipe); its acquire and the block barrier after it make the copied
+      // rows visible to every thread
+      bool ok = true;
+      if (t == 0) ok = mbar_wait(&bar[q & 1], (uint32_t)(q >> 1));
       ok = __syncthreads_and(ok);
       if (!ok) {
         // record the timeout, then give the copies in flight one more bounded
