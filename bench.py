@@ -401,10 +401,14 @@ def run_ours(args):
     # the chain record back.  The upload of step k + 1 is staged
     # (bps_stage_data_host_u16) before step k runs, so it overlaps step k; all
     # uploads and read-backs lie inside the timed region.
-    k_e2e = min(args.steps, 20)
+    k_e2e = min(args.steps, 40)
     cnt_h = torch.from_numpy(counts.astype(np.uint16)).pin_memory().numpy()   # counts <= 65535: 16-bit upload
     R_h = torch.from_numpy(R).pin_memory().numpy()
     rec_h = torch.zeros(s.rec_len, dtype=torch.float64).pin_memory().numpy()
+    # untimed warm-up of this path (the first host upload creates the copy streams)
+    for _ in range(2):
+        bps.bps_stage_data_host_u16(s.ctx, cnt_h, R_h)
+        rec_h[:] = bps.bps_gibbs_iterate(s.ctx, 1, s.rec_len)[0]
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     bps.bps_stage_data_host_u16(s.ctx, cnt_h, R_h)

@@ -1074,8 +1074,10 @@ bps_status stage_data(bps_ctx* ctx, int ch, const void* counts, const float* R, 
     }
   }
   const size_t slot_bytes = (size_t)ctx->nv * (sizeof(int32_t) + sizeof(float));
-  if (host && !ctx->stage) {
-    bool ok = cudaMalloc((void**)&ctx->stage, 2 * slot_bytes) == cudaSuccess;
+  // copy streams for host uploads; the staging buffer only for 32-bit counts
+  // (16-bit counts are copied straight into the data slot)
+  if (host && !ctx->copy_stream[0]) {
+    bool ok = true;
     for (int i = 0; i < 2 && ok; ++i)
       ok = cudaStreamCreateWithFlags(&ctx->copy_stream[i], cudaStreamNonBlocking) == cudaSuccess &&
            cudaEventCreateWithFlags(&ctx->stage_copied[i][0], cudaEventDisableTiming) == cudaSuccess &&
@@ -1084,6 +1086,13 @@ bps_status stage_data(bps_ctx* ctx, int ch, const void* counts, const float* R, 
     if (!ok) {
       cudaGetLastError();
       free_streams(ctx);
+      return fail(ctx, BPS_ENOMEM, "copy streams for the host upload could not be created");
+    }
+  }
+  if (host && !c16 && !ctx->stage) {
+    if (cudaMalloc((void**)&ctx->stage, 2 * slot_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->stage = nullptr;
       return fail(ctx, BPS_ENOMEM, "staging buffers for the host upload could not be allocated");
     }
   }

@@ -14,6 +14,8 @@
 #include "bps_tma.cuh"
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 namespace bps {
 
 enum XMode {
@@ -1309,7 +1311,7 @@ __global__ void __launch_bounds__(256) k_data(const CT* cin, const float* rin, u
 // support is a warp minimum and maximum when a warp's 128 voxels lie on one z
 // line (N a multiple of 128), else a pair of atomics per thread with data.
 template <typename CT>
-__global__ void __launch_bounds__(256) k_data4(const CT* __restrict__ cin, const float* __restrict__ rin,
+__global__ void __launch_bounds__(256, 4) k_data4(const CT* __restrict__ cin, const float* __restrict__ rin,
                                                uint16_t* cout, float* rout, long long nv, double* part, int stride,
                                                int2* span, int n_grid) {
   __shared__ double s_red[32];
@@ -1318,16 +1320,30 @@ __global__ void __launch_bounds__(256) k_data4(const CT* __restrict__ cin, const
   const long long n4 = nv / 4;
   const int lane = threadIdx.x & 31;
   const bool warp_line = n_grid % 128 == 0;
-  for (long long q = blockIdx.x * 256LL + threadIdx.x; q < n4; q += (long long)gridDim.x * 256) {
-    int c4[4];
-    if constexpr (sizeof(CT) == 2) {
-      const ushort4 cc = reinterpret_cast<const ushort4*>(cin)[q];
-      c4[0] = cc.x; c4[1] = cc.y; c4[2] = cc.z; c4[3] = cc.w;
-    } else {
-      const int4 cc = reinterpret_cast<const int4*>(cin)[q];
-      c4[0] = cc.x; c4[1] = cc.y; c4[2] = cc.z; c4[3] = cc.w;
+  // DEPTH consecutive grid-stride groups are loaded before any is processed (more
+  // loads in flight per thread); they are then processed in the order of the
+  // plain grid-stride loop, so every sum sees its terms in the same order
+  constexpr int DEPTH = sizeof(CT) == 2 ? 4 : 2;   // 16-bit counts leave room for four groups
+  using CV = typename std::conditional<sizeof(CT) == 2, ushort4, int4>::type;
+  const long long gstride = (long long)gridDim.x * 256;
+  for (long long q0 = blockIdx.x * 256LL + threadIdx.x; q0 < n4; q0 += DEPTH * gstride) {
+  CV cbuf[DEPTH];
+  float4 rbuf[DEPTH];
+#pragma unroll
+  for (int u = 0; u < DEPTH; ++u) {
+    const long long qu = q0 + u * gstride;
+    if (qu < n4) {
+      cbuf[u] = reinterpret_cast<const CV*>(cin)[qu];
+      rbuf[u] = reinterpret_cast<const float4*>(rin)[qu];
     }
-    const float4 rr = reinterpret_cast<const float4*>(rin)[q];
+  }
+#pragma unroll
+  for (int u = 0; u < DEPTH; ++u) {
+    const long long q = q0 + u * gstride;
+    if (q >= n4) break;
+    int c4[4];
+    c4[0] = (int)cbuf[u].x; c4[1] = (int)cbuf[u].y; c4[2] = (int)cbuf[u].z; c4[3] = (int)cbuf[u].w;
+    const float4 rr = rbuf[u];
     const float r4[4] = {rr.x, rr.y, rr.z, rr.w};
     unsigned short o4[4];
     float or4[4];
@@ -1370,6 +1386,7 @@ __global__ void __launch_bounds__(256) k_data4(const CT* __restrict__ cin, const
         atomicMax(&span[line].y, (hi + 3) & ~3);
       }
     }
+  }
   }
   double v0 = block_sum<256>((double)sR - (double)cR, s_red);
   double v1 = block_sum<256>((double)sB - (double)cB, s_red);
