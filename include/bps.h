@@ -523,10 +523,11 @@ int bps_z_line_pairs(const bps_ctx* ctx);
  * batch): 0 loads its tiles straight into registers; 1, 2, 3 stage them in
  * shared memory with tensor copies (W, delta and p; W and delta; W only); 4
  * streams the delta and p rows through a two-slot ring of quarter tiles filled
- * by tensor copies while W is transformed.  The five give bit-identical
+ * by tensor copies while W is transformed; 5 fills the same ring with 16-byte
+ * asynchronous copies issued by every thread.  The six give bit-identical
  * results.  Chosen when the context is created, like bps_z_line_pairs: the
- * first context of a (GPU model, grid, number of chains) kind times the five
- * and keeps the fastest, cached with the z-pass choice; BPS_XTMA = 0..4 forces
+ * first context of a (GPU model, grid, number of chains) kind times the six
+ * and keeps the fastest, cached with the z-pass choice; BPS_XTMA = 0..5 forces
  * one, BPS_AUTOTUNE=0 keeps 0. */
 int bps_x_pass_variant(const bps_ctx* ctx);
 

@@ -692,7 +692,7 @@ struct XRing {
   static_assert(QTP * sizeof(float2) % 128 == 0, "copy destinations on 128-byte boundaries");
 };
 
-template <int N>
+template <int N, bool TMA>
 __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
     k_xleap_ring(Fields fp0, XArgs xa, const __grid_constant__ XMaps maps) {
   using XR = XRing<N>;
@@ -714,19 +714,41 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
   const int cur = ds->cur;
   const int sbuf = xa.first ? cur : 1 - cur;
   const CUtensorMap* dmap = sbuf ? &maps.d1q : &maps.d0q;
-  auto issue = [&](int q) {                                 // thread 0: quarter q into slot q & 1
-    uint64_t* b = &bar[q & 1];
+  const float2* src = dsel(fp, sbuf);
+  // quarter q into slot q & 1: TMA, one thread issues two tensor copies on the
+  // slot's barrier; else every thread issues 16-byte copies (two complex of one
+  // row each, a warp covering four whole rows) in its own copy group
+  auto issue = [&](int q) {
     float2* slot = s_ring + (size_t)(q & 1) * 2 * XR::QTP;
-    mbar_expect_tx(b, XR::SLOT_BYTES);
-    tma_load_4d(slot, dmap, T.kz0, T.ky0, q * XR::QR, blockIdx.y, b);
-    tma_load_4d(slot + XR::QTP, &maps.phq, T.kz0, T.ky0, q * XR::QR, blockIdx.y, b);
+    if constexpr (TMA) {
+      uint64_t* b = &bar[q & 1];
+      mbar_expect_tx(b, XR::SLOT_BYTES);
+      tma_load_4d(slot, dmap, T.kz0, T.ky0, q * XR::QR, blockIdx.y, b);
+      tma_load_4d(slot + XR::QTP, &maps.phq, T.kz0, T.ky0, q * XR::QR, blockIdx.y, b);
+    } else {
+      constexpr int CH = XR::QT / 2;                        // 16-byte chunks of one array's quarter
+      for (int c = t; c < 2 * CH; c += NT) {
+        const int arr = c / CH, cc = c - arr * CH;
+        const int row = cc / (F / 2), pair = cc - row * (F / 2);
+        const float2* g = (arr ? fp.ph : src) + T.base + (long long)(q * XR::QR + row) * T.rs + 2 * pair;
+        cp_async16(slot + arr * XR::QTP + row * F + 2 * pair, g);
+      }
+      cp_async_commit();
+    }
   };
-  if (staged && t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_fence_init();
-    issue(0);
-    issue(1);
+  if (staged) {
+    if constexpr (TMA) {
+      if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        issue(0);
+        issue(1);
+      }
+    } else {
+      issue(0);
+      issue(1);
+    }
   }
   load_twiddles<N>(s_tw, fp.tw, t, NT);
   for (int i = t; i < MAXB; i += NT) {
@@ -745,7 +767,6 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
   const long long colo = T.base + (long long)f * T.cs;
   const bool mm = fp.mass_mode != 0;
   const float scb = bin_scale(fp.n_bins, N), scm = bin_scale(fp.n_mass, N);
-  const float2* src = dsel(fp, sbuf);
   float2* dst = dsel(fp, 1 - cur);
   float2 v[C::RMAX];
   if (ja < R1) {
@@ -760,7 +781,14 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const float2* slot = s_ring + (size_t)(q & 1) * 2 * XR::QTP;
-    if (staged) {
+    if (staged && !TMA) {
+      // this thread's copies of quarter q have landed (only quarter q + 1 may
+      // still be in flight); the barrier makes every thread's copies visible
+      if (q < 3) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      __syncthreads();
+    }
+    if (staged && TMA) {
       // one thread polls the barrier (256 pollers flood the shared-memory
       // pipe); its acquire and the block barrier after it make the copied
       // rows visible to every thread
@@ -812,8 +840,12 @@ __global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
     }
     if (staged && q + 2 < 4) {
       __syncthreads();                                      // every thread has read this slot
-      if (t == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if constexpr (TMA) {
+        if (t == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(q + 2);
+        }
+      } else {
         issue(q + 2);
       }
     }
@@ -1517,19 +1549,20 @@ XLeapTma xleap_entry() {
   return launch_xleap_tma<N, SD, SP>;
 }
 
-template <int N>
+template <int N, bool TMA>
 void launch_xleap_ring(const Fields& f, const XMaps& m, int first, int nch, cudaStream_t s) {
-  k_xleap_ring<N><<<dim3(Cfg<N>::TILES, nch), Cfg<N>::NT, XRing<N>::SMEM, s>>>(f, XArgs{-1, nullptr, first, -1}, m);
+  k_xleap_ring<N, TMA><<<dim3(Cfg<N>::TILES, nch), Cfg<N>::NT, XRing<N>::SMEM, s>>>(f, XArgs{-1, nullptr, first, -1},
+                                                                                      m);
 }
 
-template <int N>
+template <int N, bool TMA>
 XLeapTma xleap_ring_entry() {
-  if (cudaFuncSetAttribute(k_xleap_ring<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XRing<N>::SMEM) !=
-      cudaSuccess) {
+  if (cudaFuncSetAttribute(k_xleap_ring<N, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)XRing<N>::SMEM) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  return launch_xleap_ring<N>;
+  return launch_xleap_ring<N, TMA>;
 }
 
 template <int N>
@@ -1538,7 +1571,8 @@ XLeapTma xleap_variant(int which) {
     case 1: return xleap_entry<N, 1, 1>();   // W, delta and p staged (two blocks per SM)
     case 2: return xleap_entry<N, 1, 0>();   // W and delta staged (three blocks per SM)
     case 3: return xleap_entry<N, 0, 0>();   // W staged (three blocks per SM)
-    case 4: return xleap_ring_entry<N>();    // delta and p through a ring of quarters (three blocks per SM)
+    case 4: return xleap_ring_entry<N, true>();    // delta and p quarters through a ring filled by tensor copies
+    case 5: return xleap_ring_entry<N, false>();   // the same ring filled by 16-byte copies of every thread
     default: return nullptr;
   }
 }

@@ -65,6 +65,18 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared by the calling thread (both
+// addresses 16-byte aligned), in the thread's current copy group
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most `pending` of the calling thread's copy groups are still in flight
+template <int pending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(pending) : "memory");
+}
+
 // tiled tensor copy global -> shared of one box of a 4D tensor map (coordinates
 // innermost first: x, y, z, w), completing on `bar`.  The map lives in the
 // kernel's parameter space (__grid_constant__); x times the element size must
