@@ -75,6 +75,7 @@ struct bps_ctx {
   int rebuild_blocks = 0;
   int n_sm = 0;
   uint64_t launches = 0;
+  uint8_t* pbin = nullptr;   // k bin of every half-spectrum mode (Fields::pbin)
   // CUDA graph of one Gibbs iteration (captured on first use)
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
@@ -269,6 +270,7 @@ Fields fields(bps_ctx* c) {
   f.part = c->part;
   f.part_stride = c->part_stride;
   f.tw = c->tw;
+  f.pbin = c->pbin;
   f.grid_n = c->N;
   f.inv_nv = (float)(1.0 / (double)c->nv);
   f.mass_mode = (c->cfg.mass_mode != 0 || c->mnet) ? 1 : 0;
@@ -675,6 +677,7 @@ void free_all(bps_ctx* c) {
   cudaFree(c->cnt);
   cudaFree(c->R);
   cudaFree(c->tw);
+  cudaFree(c->pbin);
   cudaFree(c->part);
   cudaFree(c->ds);
   cudaFree(c->chain_dev);
@@ -979,7 +982,7 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
   bool ok = alloc((void**)&ctx->dh[0], sb) && alloc((void**)&ctx->dh[1], sb) && alloc((void**)&ctx->ph, sb) &&
             alloc((void**)&ctx->W, sb) && alloc((void**)&ctx->a, rb) && alloc((void**)&ctx->c, rb) &&
             (grid_n % 32 != 0 || alloc((void**)&ctx->span, span_bytes)) &&
-            alloc((void**)&ctx->tw, grid_n * sizeof(float2)) &&
+            alloc((void**)&ctx->tw, grid_n * sizeof(float2)) && alloc((void**)&ctx->pbin, ctx->n_spec) &&
             alloc((void**)&ctx->part, (size_t)ctx->part_cstride * B * sizeof(double)) &&
             alloc((void**)&ctx->ds, sizeof(DevState) * B) &&
             (!ids.empty() || alloc((void**)&ctx->chain_dev, (size_t)ctx->chain_cap * rec_len * sizeof(double))) &&
@@ -989,6 +992,22 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
     free_all(ctx);
     delete ctx;
     return fail(nullptr, BPS_ENOMEM, "device allocation failed");
+  }
+  // the k bin of every half-spectrum mode, from the same integer rule as the
+  // bin thresholds (255 for the DC mode and the pad column)
+  std::vector<uint8_t> pbin(ctx->n_spec, 255);
+  {
+    const int H = grid_n / 2, ZP = pt.zp;
+    std::vector<uint8_t> of_n2(3 * (size_t)H * H + 1, 255);
+    for (size_t n2 = 1; n2 < of_n2.size(); ++n2) of_n2[n2] = (uint8_t)bin_of_host((long long)n2, grid_n, cfg->n_bins);
+    for (int kx = 0; kx < grid_n; ++kx) {
+      const int nx = kx <= H ? kx : kx - grid_n;
+      for (int ky = 0; ky < grid_n; ++ky) {
+        const int ny = ky <= H ? ky : ky - grid_n;
+        uint8_t* row = pbin.data() + ((size_t)kx * grid_n + ky) * ZP;
+        for (int kz = 0; kz <= H; ++kz) row[kz] = of_n2[(size_t)(nx * nx + ny * ny + kz * kz)];
+      }
+    }
   }
   // twiddles W_N^j = exp(-2 pi i j / N), FP64 rounded to FP32
   std::vector<float2> tw(grid_n);
@@ -1003,6 +1022,7 @@ bps_status create_group(int grid_n, const std::vector<double>& box, const std::v
     hs[j].nsub = nsub[j];
   }
   cudaError_t e = cudaMemcpyAsync(ctx->tw, tw.data(), grid_n * sizeof(float2), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->pbin, pbin.data(), ctx->n_spec, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ds, hs.data(), sizeof(DevState) * B, cudaMemcpyHostToDevice, stream);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemsetAsync(ctx->dh[i], 0, sb, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ph, 0, sb, stream);

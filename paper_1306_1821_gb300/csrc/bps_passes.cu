@@ -370,11 +370,10 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
 #pragma unroll
       for (int d = 0; d < R1; ++d) v[d] = src[colo + (long long)(jc + R2 * d) * T.rs];
       if constexpr (MODE == X_JINV) {
+        // the jump's field scale by bin, the bins read from the context's map
 #pragma unroll
         for (int d = 0; d < R1; ++d) {
-          const int k = jc + R2 * d;
-          const int nx = sgn_n<N>(k);
-          const int m = bin_est(nx * nx + n2yz, s_thr, scb, fp.n_bins);
+          const int m = bin_of_map(fp.pbin, colo + (long long)(jc + R2 * d) * T.rs);
           v[d] = m >= 0 ? cscale(v[d], s_js[m]) : make_float2(0.f, 0.f);
         }
       }
@@ -392,10 +391,8 @@ __global__ void __launch_bounds__(Cfg<N>::NT, MODE == X_LEAP || MODE == X_LEAPG 
     if (act) {
 #pragma unroll
       for (int d = 0; d < R1; ++d) {
-        const int k = jc + R2 * d;
-        const int nx = sgn_n<N>(k);
-        const int m = bin_est(nx * nx + n2yz, s_thr, scb, fp.n_bins);
-        const long long idx = colo + (long long)k * T.rs;
+        const long long idx = colo + (long long)(jc + R2 * d) * T.rs;
+        const int m = bin_of_map(fp.pbin, idx);
         dsel(fp, cur)[idx] = m >= 0 ? cscale(dsel(fp, cur)[idx], s_js[m]) : make_float2(0.f, 0.f);
       }
     }

@@ -38,6 +38,9 @@ struct Fields {
   double* part;           // per-block partial sums (FP64)
   int part_stride;        // doubles between consecutive quantities of one region
   const float2* tw;       // W_N^j = exp(-2 pi i j / N), j < N (FP64-rounded)
+  // k bin of every mode, in the half-spectrum layout (255: the DC mode, the pad
+  // column); the same for every chain of a batch group (one grid, one bin layout)
+  const uint8_t* pbin;
   int grid_n;             // N
   float inv_nv;           // 1 / N^3
   int mass_mode;
@@ -200,6 +203,11 @@ __device__ __forceinline__ int bin_of(int n2, const int* thr) {
 // which is never more than one bin off for N <= 512 and nb <= 64 (checked
 // exhaustively on the host by the test suite), corrected against the exact
 // integer thresholds: two independent table reads instead of six dependent ones.
+__device__ __forceinline__ int bin_of_map(const uint8_t* pbin, long long idx) {
+  const int b = __ldg(pbin + idx);
+  return b == 255 ? -1 : b;
+}
+
 __device__ __forceinline__ float bin_scale(int nb, int N) { return (float)nb / (0.8660254f * (float)N); }
 __device__ __forceinline__ int bin_est(int n2, const int* thr, float scale, int nb) {
   if (n2 == 0) return -1;
