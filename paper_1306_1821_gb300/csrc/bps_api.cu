@@ -465,7 +465,7 @@ bps_status hmc_move(bps_ctx* ctx, bool advance) {
   P.x_final(f, region_offset(ctx, RG_FINAL), B, s);
   launch_move_end(sa, region_offset(ctx, RG_INIT), region_offset(ctx, RG_LIK0), region_offset(ctx, RG_FINAL),
                   region_offset(ctx, RG_LIK1), P.x_tiles, lik_tiles(ctx), B, s);
-  int n = 6 + L + (ctx->mnet ? 1 : 0);
+  int n = 7 + L + (ctx->mnet ? 1 : 0);   // launch_move_end is two kernels
   if (advance) {
     launch_advance(ctx->ds, B, s);
     ++n;

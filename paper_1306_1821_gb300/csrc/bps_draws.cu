@@ -59,20 +59,38 @@ __global__ void k_move_begin(ScalarArgs a0) {
 }
 
 // H = (1/2N^3) sum w (|p|^2/M + |delta|^2/lambda) + (1/2) sum (a delta^2 - 2 c delta)
-__global__ void k_move_end(ScalarArgs a0, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz) {
+// The eight sums of a move, one block each (on different SMs: each sum is a
+// chain of FP64 additions), into the chain state's scratch: K0, E0, L0, K1, E1,
+// L1, G0, G1 (the kinetic, prior and likelihood energies at the start and the
+// end, and the two force norms of the leapfrog energy identity).
+__global__ void k_move_sums(ScalarArgs a0, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz) {
   const ScalarArgs a = chain_args(a0, blockIdx.y);
   __shared__ double sh[32];
-  DevState* ds = a.ds;
   const double h = 0.5 * a.inv_nv;
-  const double K0 = sum_partials(a.part + r_init, nx, sh) * h;
-  const double E0 = sum_partials(a.part + r_init + a.stride, nx, sh) * h;
-  const double L0 = sum_partials(a.part + r_lik0, nz, sh);
-  const double K1 = sum_partials(a.part + r_final, nx, sh) * h;
-  const double E1 = sum_partials(a.part + r_final + a.stride, nx, sh) * h;
-  const double L1 = sum_partials(a.part + r_lik1, nz, sh);
-  const double G0 = sum_partials(a.part + r_init + 2 * a.stride, nx, sh) * a.inv_nv;
-  const double G1 = sum_partials(a.part + r_final + 2 * a.stride, nx, sh) * a.inv_nv;
+  const double* p = nullptr;
+  int n = nx;
+  double scale = h;
+  switch (blockIdx.x) {
+    case 0: p = a.part + r_init; break;
+    case 1: p = a.part + r_init + a.stride; break;
+    case 2: p = a.part + r_lik0; n = nz; scale = 1.0; break;
+    case 3: p = a.part + r_final; break;
+    case 4: p = a.part + r_final + a.stride; break;
+    case 5: p = a.part + r_lik1; n = nz; scale = 1.0; break;
+    case 6: p = a.part + r_init + 2 * a.stride; scale = a.inv_nv; break;
+    default: p = a.part + r_final + 2 * a.stride; scale = a.inv_nv; break;
+  }
+  const double s = sum_partials(p, n, sh);
+  if (threadIdx.x == 0) a.ds->scratch[blockIdx.x] = s * scale;
+}
+
+__global__ void k_move_end(ScalarArgs a0) {
+  const ScalarArgs a = chain_args(a0, blockIdx.y);
+  DevState* ds = a.ds;
   if (threadIdx.x == 0) {
+    const double K0 = ds->scratch[0], E0 = ds->scratch[1], L0 = ds->scratch[2];
+    const double K1 = ds->scratch[3], E1 = ds->scratch[4], L1 = ds->scratch[5];
+    const double G0 = ds->scratch[6], G1 = ds->scratch[7];
     const double H0 = K0 + E0 + L0, H1 = K1 + E1 + L1;
     // H(end) - H(start) of Eq. acceptance_rule.  The potential of the density
     // move (Eq. Wiener_Posterior_psi with fixed P, b, Nbar) is exactly quadratic
@@ -506,7 +524,8 @@ __global__ void k_mstat(ScalarArgs a0, int region, int nblk, int final_) {
 void launch_move_begin(const ScalarArgs& a, int nch, cudaStream_t s) { k_move_begin<<<dim3(1, nch), MAXB, 0, s>>>(a); }
 void launch_move_end(const ScalarArgs& a, int r_init, int r_lik0, int r_final, int r_lik1, int nx, int nz, int nch,
                      cudaStream_t s) {
-  k_move_end<<<dim3(1, nch), 256, 0, s>>>(a, r_init, r_lik0, r_final, r_lik1, nx, nz);
+  k_move_sums<<<dim3(8, nch), 256, 0, s>>>(a, r_init, r_lik0, r_final, r_lik1, nx, nz);
+  k_move_end<<<dim3(1, nch), 32, 0, s>>>(a);
 }
 void launch_power(const ScalarArgs& a, int region, int nx, int draw, int nch, cudaStream_t s) {
   k_power<<<dim3(a.n_bins, nch), 256, 0, s>>>(a, region, nx, draw);
