@@ -524,10 +524,11 @@ int bps_z_line_pairs(const bps_ctx* ctx);
  * shared memory with tensor copies (W, delta and p; W and delta; W only); 4
  * streams the delta and p rows through a two-slot ring of quarter tiles filled
  * by tensor copies while W is transformed; 5 fills the same ring with 16-byte
- * asynchronous copies issued by every thread.  The six give bit-identical
+ * asynchronous copies issued by every thread; 6 gives each warp its own rows of
+ * the ring (no block barrier per quarter).  The seven give bit-identical
  * results.  Chosen when the context is created, like bps_z_line_pairs: the
- * first context of a (GPU model, grid, number of chains) kind times the six
- * and keeps the fastest, cached with the z-pass choice; BPS_XTMA = 0..5 forces
+ * first context of a (GPU model, grid, number of chains) kind times the seven
+ * and keeps the fastest, cached with the z-pass choice; BPS_XTMA = 0..6 forces
  * one, BPS_AUTOTUNE=0 keeps 0. */
 int bps_x_pass_variant(const bps_ctx* ctx);
 

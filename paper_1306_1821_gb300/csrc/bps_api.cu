@@ -832,14 +832,15 @@ bps_status choose_zgrad(bps_ctx* ctx) {
   return BPS_OK;
 }
 
-// The leapfrog x pass has six implementations with bit-identical results: the
+// The leapfrog x pass has seven implementations with bit-identical results: the
 // direct-load pass, three with tensor-copy staged tiles (W, delta and p; W and
-// delta; W only) and two that stream delta and p through a ring of quarter
-// tiles (filled by tensor copies, or by 16-byte copies of every thread).  Which
+// delta; W only) and three that stream delta and p through a ring of quarter
+// tiles (filled by tensor copies, by 16-byte copies of every thread, or by each
+// warp for its own rows, without block barriers).  Which
 // is fastest depends on the GPU, the grid and the number of chains sharing a
 // launch, so the first context of a kind times them on its own (still empty)
 // buffers like the z-pass tiles above and caches the choice ("... xleap" keys).
-// BPS_XTMA = 0..5 forces one; BPS_AUTOTUNE=0 keeps the direct pass.
+// BPS_XTMA = 0..6 forces one; BPS_AUTOTUNE=0 keeps the direct pass.
 bps_status choose_xleap(bps_ctx* ctx) {
   ctx->xleap = nullptr;
   int which = 0;
@@ -859,7 +860,7 @@ bps_status choose_xleap(bps_ctx* ctx) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (!g_tune_loaded) tune_load();
     auto it = g_tune.find(key);
-    if (it != g_tune.end() && it->second >= 0 && it->second <= 5) {
+    if (it != g_tune.end() && it->second >= 0 && it->second <= 6) {
       which = it->second;
     } else {
       cudaStream_t s = ctx->stream;
@@ -868,7 +869,7 @@ bps_status choose_xleap(bps_ctx* ctx) {
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       float best = 1e30f;
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < 7; ++c) {
         XLeapTma fn = c ? xleap_tma(ctx->N, c) : nullptr;
         if (c && !fn) continue;
         auto run = [&] {
@@ -1523,7 +1524,7 @@ int bps_x_pass_variant(const bps_ctx* ctx) {
   if (!ctx) return -1;
   const bps_ctx* g = ctx->is_batch ? (ctx->groups.empty() ? nullptr : ctx->groups[0]) : ctx;
   if (!g || !g->xleap) return 0;
-  for (int c = 1; c <= 5; ++c)
+  for (int c = 1; c <= 6; ++c)
     if (xleap_tma(g->N, c) == g->xleap) return c;
   return 0;
 }

@@ -62,7 +62,7 @@ bool make_xmaps(const Fields& f, int N, int nch, XMaps* out);
 using XLeapTma = void (*)(const Fields&, const XMaps&, int first, int nch, cudaStream_t);
 // which: 1 stages W, delta and p; 2 W and delta; 3 W only; 4 streams delta and p
 // through a ring of quarter tiles filled by tensor copies, 5 the same ring filled
-// by 16-byte copies of every thread (0 or other: none)
+// by 16-byte copies of every thread, 6 warp-private rings (0 or other: none)
 XLeapTma xleap_tma(int N, int which);
 
 // The fused y^-1 / z / y stage of a force evaluation (bps_yz.cu): one CTA per

@@ -1209,6 +1209,140 @@ __global__ void __launch_bounds__(LP * Cfg<N>::RMAX) k_zpass(Fields fp0, ZArgs z
   }
 }
 
+// ------------------------------------------------------------------ x pass with warp-private rings
+// X_LEAP like k_xleap_ring, but each warp copies, waits for and reads only the
+// delta and p rows its own threads use (16-byte cp.async copies into the same
+// two-slot layout): the quarter loop has no block barrier, only the warp's own
+// copy-group waits and warp barriers.  Nyquist tiles read delta and p directly.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::NT, BPS_XLEAP_MIN_BLOCKS)
+    k_xleap_wring(Fields fp0, XArgs xa, const __grid_constant__ XMaps maps) {
+  using XR = XRing<N>;
+  const Fields fp = at_chain(fp0, blockIdx.y);
+  using C = Cfg<N>;
+  constexpr int F = C::F, R1 = C::R1, R2 = C::R2, NT = C::NT, HQ = R1 / 4;
+  constexpr int JW = 32 / F;                                // row groups (jc values) per warp
+  static_assert(32 % F == 0, "a warp covers whole row groups");
+  (void)maps;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* s_ring = reinterpret_cast<float2*>(smem);         // [slot][delta, p][QR rows][F], arrays QTP apart
+  __shared__ float2 s_tw[N];
+  __shared__ __align__(16) float2 s_ex[N * F];
+  __shared__ int s_thr[MAXB], s_mthr[MAXB];
+  __shared__ float s_il[MAXB], s_im[MAXB], s_ims[MAXB];
+  const int t = threadIdx.x, lane = t & 31;
+  DevState* ds = fp.ds;
+  const int id = tile_id<N>();
+  const Tile<N> T = tile_x<N>(id);
+  const bool staged = id < N * C::ZB;
+  const int cur = ds->cur;
+  const int sbuf = xa.first ? cur : 1 - cur;
+  const float2* src = dsel(fp, sbuf);
+  const int jw0 = (t / 32) * JW;                            // first row group of this warp
+  // quarter q of this warp's rows into slot q & 1: rows jc + R2 e (jc of the
+  // warp, e < HQ) of delta and p, two complex per 16-byte copy
+  auto issue = [&](int q) {
+    float2* slot = s_ring + (size_t)(q & 1) * 2 * XR::QTP;
+    constexpr int PER_ARR = JW * HQ * (F / 2);
+#pragma unroll
+    for (int i = 0; i < 2 * PER_ARR / 32; ++i) {
+      const int c = lane + 32 * i;
+      const int arr = c / PER_ARR, cc = c - arr * PER_ARR;
+      const int rl = cc / (F / 2), pair = cc - rl * (F / 2);
+      const int jc = jw0 + rl % JW, e = rl / JW;
+      if (jc < R2) {
+        const int r = jc + R2 * e;
+        const float2* g = (arr ? fp.ph : src) + T.base + (long long)(q * XR::QR + r) * T.rs + 2 * pair;
+        cp_async16(slot + arr * XR::QTP + r * F + 2 * pair, g);
+      }
+    }
+    cp_async_commit();
+  };
+  if (staged) {
+    issue(0);
+    issue(1);
+  }
+  load_twiddles<N>(s_tw, fp.tw, t, NT);
+  for (int i = t; i < MAXB; i += NT) {
+    s_thr[i] = ds->thr[i];
+    s_mthr[i] = ds->mthr[i];
+    s_il[i] = ds->inv_lambda[i];
+    s_im[i] = ds->inv_M[i];
+    s_ims[i] = ds->inv_ms[i];
+  }
+  __syncthreads();   // the transform reads the twiddles before its first barrier
+  const int f = t % F;
+  const int ja = t / F;
+  const int ky = T.ky0 + f * T.dky, kz = T.kz0 + f * T.dkz;
+  const int ny = sgn_n<N>(ky);
+  const int n2yz = ny * ny + kz * kz;
+  const long long colo = T.base + (long long)f * T.cs;
+  const bool mm = fp.mass_mode != 0;
+  const float scb = bin_scale(fp.n_bins, N), scm = bin_scale(fp.n_mass, N);
+  float2* dst = dsel(fp, 1 - cur);
+  float2 v[C::RMAX];
+  if (ja < R1) {
+#pragma unroll
+    for (int b = 0; b < R2; ++b) v[b] = fp.W[colo + (long long)(ja + R1 * b) * T.rs];
+  }
+  fft2<N, R1, R2, FWD, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
+  const int jc = t / F;
+  const bool act = jc < R2;
+  const float eps = (float)ds->eps;
+  const float ek = xa.first ? 0.5f * eps : eps;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2* slot = s_ring + (size_t)(q & 1) * 2 * XR::QTP;
+    if (staged) {
+      // this lane's copies of quarter q have landed (only quarter q + 1 may still
+      // be in flight); the warp barrier makes every lane's copies visible
+      if (q < 3) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      __syncwarp();
+    }
+    if (act) {
+#pragma unroll
+      for (int e = 0; e < HQ; ++e) {
+        const int d = q * HQ + e;
+        const int k = jc + R2 * d;
+        const long long idx = colo + (long long)k * T.rs;
+        const int r = jc + R2 * e;                          // row within the quarter
+        float2 xx = staged ? slot[r * F + f] : src[idx];
+        float2 pp = staged ? slot[XR::QTP + r * F + f] : fp.ph[idx];
+        const int nx = sgn_n<N>(k);
+        const int n2 = nx * nx + n2yz;
+        const int m = bin_est(n2, s_thr, scb, fp.n_bins);
+        if (m >= 0) {
+          const float il = s_il[m];
+          float im = s_im[m];
+          if (mm) im *= s_ims[bin_est(n2, s_mthr, scm, fp.n_mass)];
+          const float gx = fmaf(xx.x, il, v[d].x), gy = fmaf(xx.y, il, v[d].y);
+          pp.x = fmaf(-ek, gx, pp.x);
+          pp.y = fmaf(-ek, gy, pp.y);
+          const float sft = eps * im;
+          xx.x = fmaf(sft, pp.x, xx.x);
+          xx.y = fmaf(sft, pp.y, xx.y);
+        } else {
+          xx = make_float2(0.f, 0.f);
+          pp = make_float2(0.f, 0.f);
+        }
+        fp.ph[idx] = pp;
+        dst[idx] = xx;
+        v[d] = xx;
+      }
+    }
+    if (staged && q + 2 < 4) {
+      __syncwarp();                                         // every lane of the warp has read this slot
+      issue(q + 2);
+    }
+  }
+  fft2<N, R2, R1, INV, MAP_COL, F, TwSquare<N>::value>(v, s_ex, s_tw, t);
+  if (ja < R1) {
+#pragma unroll
+    for (int b = 0; b < R2; ++b) fp.W[colo + (long long)(ja + R1 * b) * T.rs] = v[b];
+  }
+}
+
 // ------------------------------------------------------------------ voxel kernels
 // Kahan-compensated FP32 running sum (s, c); the sum is s - c.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
@@ -1563,6 +1697,21 @@ XLeapTma xleap_ring_entry() {
 }
 
 template <int N>
+void launch_xleap_wring(const Fields& f, const XMaps& m, int first, int nch, cudaStream_t s) {
+  k_xleap_wring<N><<<dim3(Cfg<N>::TILES, nch), Cfg<N>::NT, XRing<N>::SMEM, s>>>(f, XArgs{-1, nullptr, first, -1}, m);
+}
+
+template <int N>
+XLeapTma xleap_wring_entry() {
+  if (cudaFuncSetAttribute(k_xleap_wring<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XRing<N>::SMEM) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return launch_xleap_wring<N>;
+}
+
+template <int N>
 XLeapTma xleap_variant(int which) {
   switch (which) {
     case 1: return xleap_entry<N, 1, 1>();   // W, delta and p staged (two blocks per SM)
@@ -1570,6 +1719,7 @@ XLeapTma xleap_variant(int which) {
     case 3: return xleap_entry<N, 0, 0>();   // W staged (three blocks per SM)
     case 4: return xleap_ring_entry<N, true>();    // delta and p quarters through a ring filled by tensor copies
     case 5: return xleap_ring_entry<N, false>();   // the same ring filled by 16-byte copies of every thread
+    case 6: return xleap_wring_entry<N>();          // warp-private rings, no block barrier per quarter
     default: return nullptr;
   }
 }

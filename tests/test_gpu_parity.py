@@ -355,7 +355,7 @@ def test_tile_autotuner_choice_and_cache(torch_cuda, tmp_path, monkeypatch):
     lp = int(out.stdout.strip().splitlines()[-1])
     xv = int(out.stdout.strip().splitlines()[-2])
     assert lp in (4, 8, 16)
-    assert xv in (0, 1, 2, 3, 4, 5)
+    assert xv in (0, 1, 2, 3, 4, 5, 6)
     cache = json.loads(path.read_text())
     assert any(k.endswith("N=8 chains=3 zpairs") and v == lp for k, v in cache.items())
     # the x-pass implementation (four with bit-identical results) is tuned and cached too

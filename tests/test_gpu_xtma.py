@@ -1,6 +1,6 @@
 """The leapfrog x pass with tensor-copy staged tiles (BPS_XTMA = 1, 2, 3) or a
-ring of quarter tiles filled by tensor copies or by every thread's 16-byte copies
-(BPS_XTMA = 4, 5)
+ring of quarter tiles filled by tensor copies, by every thread's 16-byte copies or
+by each warp for its own rows (BPS_XTMA = 4, 5, 6)
 does the arithmetic of the direct-load pass in the same order, so its chains
 must be bit-identical to the default's; and one of its HMC moves is checked
 against the FP64 oracle (Sec. 4.1, the tolerances of tests/test_gpu_parity.py)."""
@@ -37,13 +37,13 @@ def chain(pb, variant, n_iter=2):
 def test_staged_x_pass_equals_the_direct_pass(N):
     pb = Problem(N, n_sub=2, n_bins=3 if N == 8 else 8 if N < 256 else 32, n_leapfrog=4, eps_max=0.1 if N < 256 else 0.02)
     rec0, spec0 = chain(pb, 0)
-    for v in (1, 2, 3, 4, 5):
+    for v in (1, 2, 3, 4, 5, 6):
         rec, spec = chain(pb, v)
         assert np.array_equal(rec, rec0), v
         assert np.array_equal(spec, spec0), v
 
 
-@pytest.mark.parametrize("variant", [1, 4, 5])
+@pytest.mark.parametrize("variant", [1, 4, 5, 6])
 def test_staged_x_pass_hmc_move_matches_oracle(variant):
     from paper_1306_1821_gb300 import bps
     pb = Problem(32, n_sub=2, n_bins=6, n_leapfrog=6, eps_max=0.25)
