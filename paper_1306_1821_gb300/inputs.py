@@ -76,7 +76,10 @@ WORKLOADS = {
 # with Phi_* = 19.6798... (the faintest bin has Nbar = 8), and biases from the
 # luminosity law of Eq. rel_bias (b_* = 1.2, M_* = -20.83, a = 0.895,
 # b = 0.105, c = -0.040) at the bin centres.  The values below are those
-# definitions evaluated once in FP64; the DR7 mask is replaced by a 25% cap.
+# definitions evaluated once in FP64: they are the table of
+# tests/golden/schechter15.txt, which tests/golden/schechter15.py writes from
+# the printed constants with the FP64 oracle, and the tests hold the two equal.
+# The DR7 mask is replaced by a 25% cap.
 SCHECHTER15_EDGES = [-23.0 + 0.4 * i for i in range(16)]
 SCHECHTER15_PHI_STAR = 19.679837431231647
 SCHECHTER15_B = [1.9419001265076423, 1.6843806505723544, 1.5003038561471536, 1.3670369833779648,
