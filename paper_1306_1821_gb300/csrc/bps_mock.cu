@@ -234,13 +234,6 @@ struct Schechter {
     }
     return z;
   }
-  double selection(double r, double M_l, double M_u, double norm) const {
-    if (!(r > 0.0)) return 0.0;
-    const double mu = 5.0 * std::log10((1.0 + redshift(r)) * r) + 25.0;
-    const double lo = std::max(M_l, m_bright - mu), hi = std::min(M_u, m_faint - mu);
-    if (!(hi > lo)) return 0.0;
-    return integral(lo, hi) / norm;
-  }
 };
 
 }  // namespace
