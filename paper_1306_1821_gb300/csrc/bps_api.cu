@@ -693,7 +693,8 @@ void free_all(bps_ctx* c) {
 // choice is cached for the process and in a JSON file (BPS_TUNE_CACHE, else
 // $HOME/.cache/bps_tune.json) so later runs reuse it and give the same
 // chains.  BPS_AUTOTUNE=0 keeps 8 line pairs.  The choice changes only the
-// grouping of the likelihood-energy partial sums (FP64 sums of FP32 terms).
+// grouping of the likelihood-energy terms into per-block partial sums
+// (compensated FP32 pairs, one FP64 value per block).
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
