@@ -456,8 +456,9 @@ bps_status bps_schechter_tables(const bps_schechter* s, int n_sub, const double*
 bps_status bps_bias_law(int n, const double* M, double b_star, double M_star, double a, double b, double c,
                         double* b_out);
 
-/* Library version string and the text of the last error of ctx (or of the
- * last failed context-free call when ctx is NULL). */
+/* Library version string and the text of the last error of ctx (or, when ctx
+ * is NULL, of the calling thread's last failed call).  The text stays valid
+ * until the next failure on ctx (or on the calling thread). */
 const char* bps_version(void);
 const char* bps_last_error(const bps_ctx* ctx);
 

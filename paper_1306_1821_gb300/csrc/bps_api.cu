@@ -203,7 +203,8 @@ bool bins_have_modes(int N, int nb, const int* thr) {
 
 namespace {
 
-std::string g_err;
+// the last error message of the calling thread (each thread reads only its own)
+thread_local std::string g_err;
 
 // partial-sum regions (offsets in doubles into one chain's part of ctx->part)
 enum Region { RG_INIT = 0, RG_LIK0, RG_FINAL, RG_LIK1, RG_BIN, RG_SUMS, RG_RB, RG_JGRAD, RG_JLIK, RG_GRAD, RG_COUNT };

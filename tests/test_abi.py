@@ -76,3 +76,38 @@ def test_z_pass_bytes_counts_the_line_supports():
     assert total == row * (lines + N * N) + 2 * 4 * span
     assert info["lines_with_support"] == lines / (N * N)
     assert info["support_voxels"] == span / N ** 3
+    # a survey that covers every voxel costs the dense pass
+    dense = bench.z_pass_bytes(np.ones((1, N, N, N), np.float32), N)[0]
+    assert dense == info["dense_bytes"] == 2 * row * N * N + 2 * 4 * N ** 3
+
+
+def test_last_error_is_per_thread(lib):
+    # context-free calls that fail on their arguments (no GPU work): each thread
+    # reads its own failure, not the one another thread made in between
+    import ctypes
+    import threading
+
+    from paper_1306_1821_gb300 import bps
+    gate = threading.Barrier(2)
+    seen = {}
+
+    def bias_law_fails():
+        assert lib.bps_bias_law(-1, None, 1.2, -20.83, 0.895, 0.105, -0.04, None) == bps.BPS_EINVAL
+        gate.wait()          # the other thread fails now
+        gate.wait()
+        seen["a"] = lib.bps_last_error(None).decode()
+
+    def tables_fail():
+        gate.wait()
+        sp = bps.bps_schechter(-20.44, -1.05, 14.5, 17.77, 0.24)
+        assert lib.bps_schechter_tables(ctypes.byref(sp), 0, None, 1.0, 2, None, None) == bps.BPS_EINVAL
+        gate.wait()
+        seen["b"] = lib.bps_last_error(None).decode()
+
+    ts = [threading.Thread(target=bias_law_fails), threading.Thread(target=tables_fail)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(30)
+    assert seen["a"].startswith("bps_bias_law"), seen
+    assert seen["b"].startswith("bps_schechter_tables"), seen

@@ -1,6 +1,5 @@
 """Host logic of bench.py: the multi-rank aggregation (max time, summed units)
-over world_size 2 gloo ranks on CPU, the clock / traffic helpers and the
-z pass's algorithmic byte count."""
+over world_size 2 gloo ranks on CPU, and the clock / traffic helpers."""
 import os
 import socket
 
@@ -68,39 +67,3 @@ def test_traffic_is_null_when_sources_changed(tmp_path, monkeypatch):
     assert bench.read_traffic() is None
     f.write_text(f"kernel_hash = {bench.kernel_hash()}\nbytes_per_launch_full = 123\n")
     assert bench.read_traffic() == 123.0
-
-
-def test_z_pass_bytes_against_line_by_line_count():
-    """Algorithmic bytes of the force z pass, counted line by line: a z line
-    that meets the survey (R > 0 in any subsample) reads its half-spectrum row
-    of W; every line writes its row; a and c are read over the line's support,
-    from its first observed voxel rounded down to a multiple of four to its
-    last observed voxel + 1 rounded up to one (the spans the data check
-    kernel records)."""
-    import numpy as np
-
-    import bench
-    N = 16
-    rng = np.random.default_rng(3)
-    R = np.zeros((2, N, N, N), dtype=np.float32)
-    R[0][rng.random((N, N, N)) < 0.05] = 0.5
-    R[1, 3, 4, 7] = 1.0                          # a single voxel: support [4, 8)
-    R[1, 5, 5, N - 1] = 1.0                      # the line's last voxel: support ends at N
-    R[:, 9, 2, :] = 0.0                          # a line with no support
-    row = (N // 2 + 1) * 8
-    total, support = 0, 0
-    for x in range(N):
-        for y in range(N):
-            idx = np.flatnonzero((R[:, x, y, :] > 0).any(axis=0))
-            total += row                                 # W written
-            if idx.size:
-                lo, hi = (idx[0] // 4) * 4, -(-(idx[-1] + 1) // 4) * 4
-                assert lo <= idx[0] and hi > idx[-1] and hi <= N
-                total += row + 2 * 4 * (hi - lo)         # W read, a and c over [lo, hi)
-                support += hi - lo
-    got, info = bench.z_pass_bytes(R, N)
-    assert got == total
-    assert info["support_voxels"] == support / N ** 3
-    assert info["dense_bytes"] == 2 * row * N * N + 2 * 4 * N ** 3
-    # a survey that covers every voxel costs the dense pass
-    assert bench.z_pass_bytes(np.ones((1, N, N, N), np.float32), N)[0] == info["dense_bytes"]
