@@ -1,4 +1,4 @@
-"""Pins of the oracle's conditional samplers (Secs. 3.4-3.6, 4.2, 4.3, Apps. A-C)."""
+"""Pins of the oracle's conditional samplers (Secs. 3.4-3.6, 4.2, 4.3, Apps. A-C), the jump with one and two bins."""
 import math
 
 import numpy as np
@@ -150,6 +150,66 @@ def test_jump_leaves_conditional_of_P_invariant():
     # the whitened field is unchanged by the jumps
     u0 = dh0 / math.sqrt(P0[0])
     assert np.allclose(dh / math.sqrt(P[0]), u0, atol=1e-10)
+
+
+def test_jump_two_bins_samples_the_conditional_of_P():
+    # 4^3 grid, two bins, flat prior alpha = 0 (proper in both tails, so the
+    # (alpha - 1) terms of the jump are exercised).  With the whitened field u
+    # fixed, delta_hat_k(theta) = delta_hat0_k sqrt(exp(theta_m(k)) / P0_m(k))
+    # (Eq. det_trans) and p(theta | u, d) ~ exp((1 - alpha) sum theta -
+    # lik(delta(theta))) (Eq. spec_posterior_MIXING_1): written out here with
+    # numpy's inverse FFT, apart from the oracle's jump code, on a 2-D grid of
+    # (theta_0, theta_1).  A chain of jumps must reproduce its means, variances
+    # and correlation.
+    wl, g, d, counts, R = survey(N=4, n_sub=1, n_bins=2, seed=5, f_sky=0.9)
+    a, c = model.local_fields(counts, R, np.array(wl.b), np.array(wl.nbar))
+    abar = a.mean()
+    alpha = 0.0
+    P0 = inputs.bin_centre_spectrum(4, wl.box, 2)
+    lnP0 = np.log(P0)
+    dh0 = grid.forward(d)
+    dh0[0, 0, 0] = 0
+    n = 201
+    t0 = np.linspace(lnP0[0] - 9.0, lnP0[0] + 3.0, n)
+    t1 = np.linspace(lnP0[1] - 9.0, lnP0[1] + 3.0, n)
+    T0, T1 = np.meshgrid(t0, t1, indexing="ij")
+    s0 = np.exp(0.5 * (T0 - lnP0[0]))[..., None, None, None]
+    s1 = np.exp(0.5 * (T1 - lnP0[1]))[..., None, None, None]
+    scale = np.where(g.bin == 0, s0, np.where(g.bin == 1, s1, 0.0))
+    delta = np.fft.irfftn(dh0 * scale, s=(4, 4, 4), axes=(-3, -2, -1))
+    lik = 0.5 * np.sum(a * delta * delta - 2.0 * c * delta, axis=(-3, -2, -1))
+    logp = (1.0 - alpha) * (T0 + T1) - lik
+    edge = max(logp[0].max(), logp[-1].max(), logp[:, 0].max(), logp[:, -1].max())
+    assert logp.max() - edge > 12.0                     # the grid holds the whole mass
+    w = np.exp(logp - logp.max())
+
+    def expect(f):
+        return integrate.trapezoid(integrate.trapezoid(w * f, t1, axis=1), t0)
+
+    Z = expect(1.0)
+    m = np.array([expect(T0), expect(T1)]) / Z
+    v = np.array([expect((T0 - m[0]) ** 2), expect((T1 - m[1]) ** 2)]) / Z
+    r = expect((T0 - m[0]) * (T1 - m[1])) / Z / math.sqrt(v[0] * v[1])
+    dh, P = dh0.copy(), P0.copy()
+    out, acc = [], 0
+    for it in range(3200):
+        dh, P, info = gibbs.jump_move(g, dh, P, a, c, abar, alpha, 6, 0.5, 21, it, P_ref=P0)
+        acc += info["accepted"]
+        out.append(np.log(P))
+    out = np.array(out[200:])
+    assert acc > 2500
+    nb = 20
+    for k in range(2):
+        x = out[:, k]
+        bm = x[: (len(x) // nb) * nb].reshape(nb, -1).mean(1)
+        se = bm.std(ddof=1) / math.sqrt(nb)
+        assert abs(x.mean() - m[k]) < 4.5 * se, (k, x.mean(), m[k], se)
+        assert x.var() == pytest.approx(v[k], rel=0.15)
+    assert abs(np.corrcoef(out[:, 0], out[:, 1])[0, 1] - r) < 0.1
+    # the whitened field is unchanged by the jumps
+    lam = np.where(g.bin >= 0, P[np.maximum(g.bin, 0)], 1.0)
+    lam0 = np.where(g.bin >= 0, P0[np.maximum(g.bin, 0)], 1.0)
+    assert np.allclose(dh / np.sqrt(lam), dh0 / np.sqrt(lam0), atol=1e-10)
 
 
 def test_jump_gradient_matches_finite_differences():
