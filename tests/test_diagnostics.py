@@ -36,3 +36,21 @@ def test_marginal_2d_is_a_density_and_ess_of_white_noise():
     for i in range(1, z.size):
         z[i] = 0.9 * z[i - 1] + e[i]
     assert abs(z.size / diagnostics.ess_geyer(z) / 19.0 - 1.0) < 0.15
+
+
+def test_autocorr_against_lag_sums_and_correlation_length_of_ar1():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(257)
+    y = x - x.mean()
+    v = np.dot(y, y) / x.size
+    direct = np.array([np.dot(y[: x.size - n], y[n:]) / x.size / v for n in range(40)])
+    assert np.allclose(diagnostics.autocorr(x, 39), direct, rtol=0, atol=1e-12)
+    assert np.all(diagnostics.autocorr(np.full(50, 3.0), 5) == 1.0)     # no variance
+    # AR(1) with coefficient 0.8: C_n = 0.8^n, below 0.1 first at n = 11
+    z = np.empty(200000)
+    z[0] = 0.0
+    e = rng.standard_normal(z.size)
+    for i in range(1, z.size):
+        z[i] = 0.8 * z[i - 1] + e[i]
+    assert np.allclose(diagnostics.autocorr(z, 12), 0.8 ** np.arange(13), atol=0.02)
+    assert diagnostics.correlation_length(z) == 11
