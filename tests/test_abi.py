@@ -1,4 +1,5 @@
-"""The C-ABI library loads and exports every entry point include/bps.h declares
+"""The C-ABI library loads and exports every entry point include/bps.h declares,
+and the ctypes binding matches every prototype and struct of the header
 (no compute: runs without a GPU)."""
 import os
 import re
@@ -111,3 +112,77 @@ def test_last_error_is_per_thread(lib):
         t.join(30)
     assert seen["a"].startswith("bps_bias_law"), seen
     assert seen["b"].startswith("bps_schechter_tables"), seen
+
+
+def _header_without_comments():
+    txt = open(os.path.join(ROOT, "include", "bps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    return "\n".join(ln for ln in txt.splitlines() if not ln.lstrip().startswith("#"))
+
+
+_SCALAR = {"int": "c_int", "double": "c_double", "float": "c_float", "uint64_t": "c_uint64", "size_t": "c_size_t",
+           "bps_status": "c_int"}
+
+
+def _scalar(t):
+    """(bytes, 'f' | 'i' | 'u') of a ctypes scalar type: c_uint64 and c_size_t
+    are one class on LP64 systems, so types are compared by width and kind."""
+    import ctypes
+    if t in (ctypes.c_float, ctypes.c_double):
+        return ctypes.sizeof(t), "f"
+    return ctypes.sizeof(t), "u" if t(-1).value > 0 else "i"
+
+
+def _kind_of_c(decl):
+    """'pointer', 'char_p' or the (width, kind) of a C parameter / return type."""
+    import ctypes
+    decl = decl.replace("const ", "").strip()
+    if "*" in decl:
+        return "char_p" if re.fullmatch(r"char\s*\*", decl) else "pointer"
+    return _scalar(getattr(ctypes, _SCALAR[decl.split()[0]]))
+
+
+def _kind_of_ctypes(t):
+    import ctypes
+    if t is None:
+        return "void"
+    if t is ctypes.c_char_p:
+        return "char_p"
+    if t is ctypes.c_void_p or issubclass(t, ctypes._Pointer):
+        return "pointer"
+    return _scalar(t)
+
+
+def test_binding_signatures_match_the_header():
+    # every prototype's arity, argument kinds (pointer or the exact scalar width)
+    # and return type against the binding's ctypes declarations
+    from paper_1306_1821_gb300 import bps
+    txt = _header_without_comments()
+    protos = re.findall(r"([A-Za-z_][\w\s\*]*?)\b(bps_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", txt)
+    assert len(protos) == len(declared())
+    for ret, name, params in protos:
+        argtypes, restype = bps._SIGS[name]
+        params = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        want = [_kind_of_c(re.sub(r"\b\w+$", "", p)) for p in params]
+        got = [_kind_of_ctypes(t) for t in argtypes]
+        assert got == want, (name, got, want)
+        r = ret.strip()
+        assert _kind_of_ctypes(restype) == ("void" if r == "void" else _kind_of_c(r)), name
+
+
+def test_binding_structs_match_the_header():
+    import ctypes
+
+    from paper_1306_1821_gb300 import bps
+    txt = _header_without_comments()
+    structs = dict((name, body) for body, name in re.findall(r"typedef struct\s*\{([^}]*)\}\s*(\w+)\s*;", txt))
+    assert set(structs) == {"bps_config", "bps_move_info", "bps_schechter"}
+    for name, body in structs.items():
+        fields = [f.strip().rsplit(None, 1) for f in body.split(";") if f.strip()]
+        cls = getattr(bps, name)
+        assert [n for _, n in fields] == [n for n, _ in cls._fields_], name
+        assert [_kind_of_c(t) for t, _ in fields] == [_kind_of_ctypes(t) for _, t in cls._fields_], name
+    # the C layout of the configuration: natural alignment, 64 bytes
+    assert ctypes.sizeof(bps.bps_config) == 64
+    assert bps.bps_config.seed.offset == 56
