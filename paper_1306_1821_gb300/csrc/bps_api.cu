@@ -16,6 +16,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <nvtx3/nvToolsExt.h>
 #include <string>
 #include <vector>
 
@@ -205,6 +206,16 @@ namespace {
 
 // the last error message of the calling thread (each thread reads only its own)
 thread_local std::string g_err;
+
+// A named NVTX range over a public call or a set-up phase: a profiler's timeline
+// shows it around the call's host work and launches; without a tool attached
+// the push and pop do nothing.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // partial-sum regions (offsets in doubles into one chain's part of ctx->part)
 enum Region { RG_INIT = 0, RG_LIK0, RG_FINAL, RG_LIK1, RG_BIN, RG_SUMS, RG_RB, RG_JGRAD, RG_JLIK, RG_GRAD, RG_COUNT };
@@ -751,6 +762,7 @@ void tune_save() {
 }
 
 bps_status choose_zgrad(bps_ctx* ctx) {
+  TraceRange trace_("bps autotune: force z tiles");
   int pick = 1;   // 8 line pairs
   const char* e = std::getenv("BPS_AUTOTUNE");
   if (!(e && std::atoi(e) == 0)) {
@@ -844,6 +856,7 @@ bps_status choose_zgrad(bps_ctx* ctx) {
 // buffers like the z-pass tiles above and caches the choice ("... xleap" keys).
 // BPS_XTMA = 0..6 forces one; BPS_AUTOTUNE=0 keeps the direct pass.
 bps_status choose_xleap(bps_ctx* ctx) {
+  TraceRange trace_("bps autotune: x pass");
   ctx->xleap = nullptr;
   int which = 0;
   const char* xe = std::getenv("BPS_XTMA");
@@ -1284,6 +1297,7 @@ bps_status get_state_chain(bps_ctx* ctx, int ch, float* delta_dev, double* P, do
 // holds event-record nodes around the leapfrog kernels of top (one group).
 bps_status capture_iteration(bps_ctx* top, const std::vector<bps_ctx*>& groups, double* rec_dev, int rec_len,
                              long long iter_stride, bool jump, bool prof, cudaGraphExec_t* out, uint64_t* launches) {
+  TraceRange trace_(prof ? "bps graph capture (profiled)" : "bps graph capture");
   bps_ctx* ctx = top;
   cudaStream_t s = top->stream;
   // capture on a private stream (the caller's may be the legacy default
@@ -1559,6 +1573,7 @@ bps_status bps_profile_read(bps_ctx* ctx, double* ms, uint64_t* n) {
 
 bps_status bps_create(int grid_n, double box_len, int n_sub, const bps_config* cfg, void* cuda_stream,
                       bps_ctx** out) {
+  TraceRange trace_("bps_create");
   if (!out || !cfg) return fail(nullptr, BPS_EINVAL, "null argument");
   *out = nullptr;
   if (n_sub < 1 || n_sub > MAXS) return fail(nullptr, BPS_EINVAL, "n_sub must be in 1..16");
@@ -1574,21 +1589,25 @@ void bps_destroy(bps_ctx* ctx) {
 }
 
 bps_status bps_set_data(bps_ctx* ctx, const int32_t* counts_dev, const float* R_dev) {
+  TraceRange trace_("bps_set_data");
   if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
   return set_data_chain(ctx, 0, counts_dev, R_dev, false);
 }
 
 bps_status bps_set_data_host(bps_ctx* ctx, const int32_t* counts, const float* R) {
+  TraceRange trace_("bps_set_data_host");
   if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
   return set_data_chain(ctx, 0, counts, R, true);
 }
 
 bps_status bps_set_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R) {
+  TraceRange trace_("bps_set_data_host_u16");
   if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
   return set_data_chain(ctx, 0, counts, R, true, true);
 }
 
 bps_status bps_stage_data_host_u16(bps_ctx* ctx, const uint16_t* counts, const float* R) {
+  TraceRange trace_("bps_stage_data_host_u16");
   if (!ctx || ctx->is_batch) return fail(ctx, BPS_EINVAL, "single-chain call on a null or batch context");
   return stage_data(ctx, 0, counts, R, true, true);
 }
@@ -1645,6 +1664,7 @@ size_t chain_blob_bytes(const bps_ctx* ctx) {
 }  // namespace
 
 bps_status bps_save_chain(bps_ctx* ctx, void* blob, size_t* bytes) {
+  TraceRange trace_("bps_save_chain");
   if (!ctx || ctx->is_batch || !bytes) return fail(ctx, BPS_EINVAL, "null argument or batch context");
   const size_t need = chain_blob_bytes(ctx);
   if (!blob) {
@@ -1683,6 +1703,7 @@ bps_status bps_save_chain(bps_ctx* ctx, void* blob, size_t* bytes) {
 }
 
 bps_status bps_load_chain(bps_ctx* ctx, const void* blob, size_t bytes) {
+  TraceRange trace_("bps_load_chain");
   if (!ctx || ctx->is_batch || !blob) return fail(ctx, BPS_EINVAL, "null argument or batch context");
   ChainHeader h;
   if (bytes < sizeof h) return fail(ctx, BPS_EINVAL, "not a chain checkpoint (too short)");
@@ -1769,6 +1790,7 @@ bps_status mock_result(bps_ctx* ctx, bps_status st) {
 }  // namespace
 
 bps_status bps_mock_field(bps_ctx* ctx, uint64_t seed, const double* P_n2, float* delta_dev) {
+  TraceRange trace_("bps_mock_field");
   MockView v;
   Fields f;
   bps_status st = mock_view(ctx, &v, &f);
@@ -1779,6 +1801,7 @@ bps_status bps_mock_field(bps_ctx* ctx, uint64_t seed, const double* P_n2, float
 
 bps_status bps_mock_counts(bps_ctx* ctx, uint64_t seed, const float* delta_dev, const float* R_dev, const double* b,
                            const double* nbar, int noise, int32_t* counts_dev) {
+  TraceRange trace_("bps_mock_counts");
   MockView v;
   Fields f;
   bps_status st = mock_view(ctx, &v, &f);
@@ -1790,6 +1813,7 @@ bps_status bps_mock_counts(bps_ctx* ctx, uint64_t seed, const float* delta_dev, 
 
 bps_status bps_mock_response(bps_ctx* ctx, double f_sky, const double* axis, int n_r, const double* table,
                              float* R_dev) {
+  TraceRange trace_("bps_mock_response");
   MockView v;
   Fields f;
   bps_status st = mock_view(ctx, &v, &f);
@@ -1858,6 +1882,7 @@ bps_status bps_selftest_wait(bps_ctx* ctx, uint64_t limit_ns) {
 }
 
 bps_status bps_hmc_step(bps_ctx* ctx, bps_move_info* info) {
+  TraceRange trace_("bps_hmc_step");
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   st = hmc_move(ctx, true);
@@ -1879,6 +1904,7 @@ bps_status bps_hmc_step(bps_ctx* ctx, bps_move_info* info) {
 
 bps_status bps_adapt_step_size(bps_ctx* ctx, int n_rounds, int moves_per_round, double target,
                                double* eps_max_out) {
+  TraceRange trace_("bps_adapt_step_size");
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   if (n_rounds < 1 || moves_per_round < 1 || !(target > 0.0 && target < 1.0))
@@ -1911,6 +1937,7 @@ bps_status bps_adapt_step_size(bps_ctx* ctx, int n_rounds, int moves_per_round, 
 }
 
 bps_status bps_sample_power(bps_ctx* ctx, double* P_out, double* sigma_out) {
+  TraceRange trace_("bps_sample_power");
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   st = power_stage(ctx, true, true);
@@ -1923,6 +1950,7 @@ bps_status bps_sample_power(bps_ctx* ctx, double* P_out, double* sigma_out) {
 }
 
 bps_status bps_sample_bias_norm(bps_ctx* ctx, double* b_out, double* nbar_out, double* sums_out) {
+  TraceRange trace_("bps_sample_bias_norm");
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   st = bias_stage(ctx, true);
@@ -1941,6 +1969,7 @@ bps_status bps_sample_bias_norm(bps_ctx* ctx, double* b_out, double* nbar_out, d
 }
 
 bps_status bps_jump(bps_ctx* ctx, bps_move_info* info) {
+  TraceRange trace_("bps_jump");
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   if (ctx->cfg.jump_leapfrog < 1 || !(ctx->cfg.jump_eps_max > 0.0))
@@ -1963,6 +1992,7 @@ bps_status bps_jump(bps_ctx* ctx, bps_move_info* info) {
 }
 
 bps_status bps_gibbs_iterate(bps_ctx* ctx, int n_iter, double* chain_out) {
+  TraceRange trace_("bps_gibbs_iterate");
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   if (n_iter < 0) return fail(ctx, BPS_EINVAL, "n_iter must be >= 0");
@@ -2006,6 +2036,7 @@ bps_status bps_set_mass_scale(bps_ctx* ctx, int n_mass_bins, const double* scale
 
 bps_status bps_set_mass_net(bps_ctx* ctx, const bps_mlp* net, const float* feat_mean, const float* feat_std,
                             double log_clamp) {
+  TraceRange trace_("bps_set_mass_net");
   if (!ctx) return fail(nullptr, BPS_EINVAL, "null context");
   std::vector<bps_ctx*> gs = ctx->is_batch ? ctx->groups : std::vector<bps_ctx*>{ctx};
   drop_graph(ctx);
@@ -2061,6 +2092,7 @@ bps_status bps_set_mass_net(bps_ctx* ctx, const bps_mlp* net, const float* feat_
 // means and standard deviations (float [width 0] each), parameters (float,
 // layout of bps_mlp_set_params); host byte order.
 bps_status bps_set_preconditioner(bps_ctx* ctx, const void* blob, size_t bytes) {
+  TraceRange trace_("bps_set_preconditioner");
   if (!ctx || !blob) return fail(ctx, BPS_EINVAL, "null argument");
   const unsigned char* b = static_cast<const unsigned char*>(blob);
   auto rd32 = [&](size_t off) {
@@ -2145,6 +2177,7 @@ bps_status bps_fft_c2r(bps_ctx* ctx, const float* spec_dev, float* real_dev) {
 }
 
 bps_status bps_gradient(bps_ctx* ctx, float* grad_dev, double* energies) {
+  TraceRange trace_("bps_gradient");
   bps_status st = need_data(ctx);
   if (st != BPS_OK) return st;
   if (!grad_dev) return fail(ctx, BPS_EINVAL, "null argument");
@@ -2173,6 +2206,7 @@ bps_status bps_gradient(bps_ctx* ctx, float* grad_dev, double* energies) {
 // ------------------------------------------------------------------ batches
 bps_status bps_create_batch(int n_chains, const int* grid_n, const double* box_len, const int* n_sub,
                             const bps_config* cfg, void* cuda_stream, bps_ctx** out) {
+  TraceRange trace_("bps_create_batch");
   if (!out || !cfg || !grid_n || !box_len || !n_sub) return fail(nullptr, BPS_EINVAL, "null argument");
   *out = nullptr;
   if (n_chains < 1) return fail(nullptr, BPS_EINVAL, "n_chains must be >= 1");
@@ -2258,6 +2292,7 @@ bps_status bps_batch_get_chain(bps_ctx* batch, int chain, float* delta_dev, doub
 }
 
 bps_status bps_batch_gibbs_iterate(bps_ctx* batch, int n_iter, double* chain_out) {
+  TraceRange trace_("bps_batch_gibbs_iterate");
   if (!batch || !batch->is_batch) return fail(batch, BPS_EINVAL, "not a batch context");
   if (n_iter < 0) return fail(batch, BPS_EINVAL, "n_iter must be >= 0");
   for (bps_ctx* g : batch->groups)
@@ -2288,6 +2323,7 @@ bps_status bps_batch_gibbs_iterate(bps_ctx* batch, int n_iter, double* chain_out
 }
 
 bps_status bps_mass_stats(bps_ctx* ctx, int n_moves, int n_mass_bins, double* out) {
+  TraceRange trace_("bps_mass_stats");
   if (!ctx || !out) return fail(ctx, BPS_EINVAL, "null argument");
   if (n_moves < 2) return fail(ctx, BPS_EINVAL, "n_moves must be >= 2");
   if (n_mass_bins < 1 || n_mass_bins > MAXB) return fail(ctx, BPS_EINVAL, "n_mass_bins must be in 1..64");
@@ -2314,6 +2350,7 @@ bps_status bps_mass_stats(bps_ctx* ctx, int n_moves, int n_mass_bins, double* ou
 }
 
 bps_status bps_window_power(bps_ctx* ctx, double* out) {
+  TraceRange trace_("bps_window_power");
   if (!ctx || !out) return fail(ctx, BPS_EINVAL, "null argument");
   if (!ctx->is_batch) {
     bps_status st = need_data(ctx);
