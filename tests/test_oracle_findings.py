@@ -6,6 +6,8 @@ small synthetic survey).
     the power spectrum, most strongly on large scales (b and P are degenerate
     through the product b^2 P that one subsample's data constrain; a second
     subsample whose bias is held fixed only breaks the degeneracy in part).
+  * Sec. 6.1 and Fig. 4: from b = Nbar = 1 and P a hundred times too large the
+    chain drifts to the true values (burn-in).
 
 On an 8^3 survey with two subsamples (the first bias fixed), two bins, the jump
 on and 1500 Gibbs iterations, the correlation of the free bias with ln P of the
@@ -33,3 +35,26 @@ def test_free_bias_is_anticorrelated_with_large_scale_power():
     assert np.all(b[:, 0] == wl.b[0])                   # the gauge: the first bias is held
     assert np.std(b[:, 1]) > 0
     assert np.corrcoef(b[:, 1], np.log(P[:, 0]))[0, 1] < -0.2
+
+
+def test_burn_in_drifts_from_the_papers_start_to_the_truth():
+    # Sec. 6.1 and Fig. 4: started from b = Nbar = 1 and P two orders of
+    # magnitude above the truth (the first bias held at its true value as the
+    # gauge), the chain drifts towards the true values.  Measured over three
+    # seeds: late means |ln(P / P_true)| <= 1.3, Nbar within 30%, b within 20%.
+    N, n_it = 8, 600
+    wl = inputs.small_workload(N, n_bins=2, n_sub=2, f_sky=0.5, seed=3)
+    _, counts, R = inputs.make_survey(wl)
+    g = grid.Geometry(N, wl.box, 2)
+    Pt = inputs.bin_centre_spectrum(N, wl.box, 2)
+    ch = gibbs.Chain(g, counts, R, 100.0 * Pt, [wl.b[0], 1.0], [1.0, 1.0], alpha=1.0, n_leapfrog=10,
+                     eps_max=0.3, jump=True, jump_leapfrog=10, jump_eps_max=0.15, fixed_bias=0, seed=103)
+    recs = [ch.iterate() for _ in range(n_it)]
+    lnP = np.log(np.array([r["P"] for r in recs]) / Pt)
+    b = np.array([r["b"] for r in recs])[:, 1]
+    nbar = np.array([r["nbar"] for r in recs])
+    assert np.all(lnP[:20] > 3.0)                       # still near the start early on
+    late = slice(n_it // 2, None)
+    assert np.all(np.abs(lnP[late].mean(0)) < 2.0)
+    assert np.all(np.abs(nbar[late].mean(0) / np.array(wl.nbar) - 1.0) < 0.4)
+    assert abs(b[late].mean() / wl.b[1] - 1.0) < 0.3
