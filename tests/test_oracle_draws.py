@@ -94,3 +94,19 @@ def test_gig_bounds_enclose_the_region():
         vs = (ys - m) * np.exp(0.5 * np.array([draws._gig_logh(y, lam, omega, m) for y in ys]))
         assert vs.max() <= vp * (1 + 1e-9)
         assert vs.min() >= vm * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("lam,omega", [(2.5, 0.7), (1.0, 3.0), (0.3, 1.5), (-4.0, 0.2), (-2.0e5, 40.0),
+                                       (1.0 - 5.0e5, 2.0e3)])
+def test_gig_mode_maximises_the_density(lam, omega):
+    # h(y) = y^(lam-1) exp(-omega (y + 1/y) / 2): the mode solves
+    # (lam - 1) / y - omega (1 - 1/y^2) / 2 = 0 (both branches of the closed form,
+    # the second free of cancellation for lam << 0, where the N-bar draw lives)
+    m = draws.gig_mode(lam, omega)
+    assert m > 0
+    dlog = (lam - 1.0) / m - 0.5 * omega * (1.0 - 1.0 / m ** 2)
+    assert abs(dlog) <= 1e-10 * (abs(lam - 1.0) / m + omega * (1.0 + 1.0 / m ** 2))
+    # brute force: the log density on a fine log-spaced grid around it peaks there
+    y = m * np.exp(np.linspace(-0.5, 0.5, 20001))
+    logh = (lam - 1.0) * np.log(y) - 0.5 * omega * (y + 1.0 / y)
+    assert abs(y[np.argmax(logh)] / m - 1.0) < 1e-4

@@ -77,3 +77,17 @@ def test_streams_are_distinct():
     d = philox.voxel_normals(2, 0, 1, 0, 64)
     for x in (b, c, d):
         assert not np.allclose(a, x)
+
+
+def test_normal64_law_and_bound():
+    # FP64 Box-Muller cosine branch from two words: standard normal, and
+    # bounded by sqrt(-2 ln u) at the smallest uniform52 value 2^-53
+    w = philox.words(3, 1, 5, 0, np.arange(1 << 15, dtype=np.uint64))
+    z = philox.normal64(w[0], w[1])
+    assert abs(z.mean()) < 5.0 / np.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5.0 * np.sqrt(2.0 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert np.max(np.abs(z)) <= np.sqrt(-2.0 * np.log(2.0 ** -53))
+    # the definition: u1 from the first word sets the radius, u2 from the second the angle
+    u1, u2 = philox.uniform52(w[0][:8]), philox.uniform52(w[1][:8])
+    assert np.array_equal(z[:8], np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2))
