@@ -225,3 +225,22 @@ def test_jump_gradient_matches_finite_differences():
         fp = gibbs.jump_potential_grad(g, dh0, P0, th + e, a, c, 0.5)[0]
         fm = gibbs.jump_potential_grad(g, dh0, P0, th - e, a, c, 0.5)[0]
         assert gr[m] == pytest.approx((fp - fm) / 2e-5, rel=1e-6, abs=1e-8)
+
+
+def test_jump_mass_depends_on_P_only_through_the_whitened_field():
+    # the jump moves (delta_hat, P) along delta_hat_k ~ sqrt(P_m(k)) with u fixed
+    # (Eq. det_trans); its HMC stays reversible only if the mass is the same at
+    # every point of that line, i.e. a function of u (and the fixed P_ref) alone
+    wl, g, d, counts, R = survey(N=8, n_sub=1, n_bins=3, seed=4)
+    a, _ = model.local_fields(counts, R, np.array(wl.b), np.array(wl.nbar))
+    abar = a.mean()
+    dh = grid.forward(d)
+    P = inputs.bin_centre_spectrum(8, wl.box, 3)
+    P_ref = P * np.array([1.3, 0.7, 2.0])
+    mu = gibbs.jump_mass(g, dh, P, P_ref, abar)
+    assert np.all(mu >= 1.0) and np.any(mu > 1.0)
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        P2 = P * np.exp(rng.uniform(-2.0, 2.0, 3))
+        dh2 = gibbs.jump_field(g, dh, P, np.log(P2))
+        assert np.allclose(gibbs.jump_mass(g, dh2, P2, P_ref, abar), mu, rtol=1e-12, atol=0)
