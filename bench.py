@@ -264,8 +264,8 @@ def run_reference(args):
         "config": config_dict(wl, "cpu"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{steps} trajectories of {L} leapfrog steps ({L + 1} force evaluations each) "
-                                   f"at 256^3 with 6 subsamples, numpy FP64 FFT, one thread, after {warm} "
-                                   f"warm-up", **host_info()},
+                                   f"at {wl.N}^3 with {wl.n_sub} subsamples, numpy FP64 FFT, one thread, "
+                                   f"after {warm} warm-up", **host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

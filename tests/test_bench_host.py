@@ -69,31 +69,32 @@ def test_traffic_is_null_when_sources_changed(tmp_path, monkeypatch):
     assert bench.read_traffic() == 123.0
 
 
-def test_reference_arm_prints_the_contract_line():
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
     # bench.py --impl reference times the FP64 oracle on the host (no GPU): one
     # JSON line with the arm's metric, unit and direction, a cpu_baseline that
     # describes the run and an e2e object with no host-device bytes; a rank
-    # other than 0 under torchrun exits 0 without work
+    # other than 0 under torchrun exits 0 without work.  Run in process on the
+    # 32^3 survey (the bench's own 256^3 survey takes minutes to set up here).
     import json
-    import subprocess
-    import sys
 
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
-    cmd = [sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"]
-    r = subprocess.run(cmd, cwd=root, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 0, r.stderr[-2000:]
-    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(bench, "WORKLOAD", "survey32")
+    argv = ["--impl", "reference", "--steps", "1", "--warmup", "0"]
+    assert bench.main(argv) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     line = json.loads(lines[0])
-    import bench
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["higher_is_better"] is True and line["value"] > 0 and line["steps"] == 1
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
-    assert line["config"]["workload"].startswith("survey256")
-    r1 = subprocess.run(cmd, cwd=root, env=dict(env, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"),
-                        capture_output=True, text=True, timeout=120)
-    assert r1.returncode == 0 and not r1.stdout.strip()
+    assert line["config"]["workload"].startswith("survey32") and "at 32^3 with 1 subsamples" in cb["sample"]
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert bench.main(argv) == 0
+    assert not capsys.readouterr().out.strip()
